@@ -1,0 +1,467 @@
+"""CPU oracle for the batched RGF selected inversion.  TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark may
+import this module; the library path never does.  It shares no code with the
+CUDA path: everything here is plain numpy complex128, written from the
+paper's statement of the problem:
+
+  * Eq. (1):  C^R = (A - B^R)^{-1}.  For electrons
+              G^R(E) = (z S - H - Sigma^R_OBC - Sigma^R_scat)^{-1}, z = E + i eta.
+  * Eq. (2):  (C^R)^{-1} C^< (C^R)^{-H} = B^<,  i.e.  G^< = G^R Sigma^< G^A.
+  * Sec. II:  A and B are block-tridiagonal; only the entries of C on that
+              pattern (diagonal and first off-diagonal blocks) are wanted, and
+              every energy is independent.
+
+The primary functions are the plain definitions (dense inversion of the full
+N x N matrix, then the block extraction).  ``rgf_blocks`` is the textbook
+recursive Green's function (the RGF the paper cites in Sec. II) as a plain
+block loop; it exists to reach sizes the dense inverse cannot, and is pinned
+to the dense definition by the tests.
+
+The open-boundary term (Sec. II: "an open boundary condition term not shown
+here") is not written out in the paper.  It is computed here by the
+Lopez Sancho - Lopez Sancho - Rubio decimation (J. Phys. F 15, 851 (1985)),
+written in A-form; pinned by the closed-form 1D-chain surface function and a
+long finite chain.  Parity: all functions below are pinned (see the oracle
+tests).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "dense_matrix", "dense_H_S", "lead_A_blocks", "sancho_rubio", "surface_residual",
+    "lead_self_energies", "lead_lesser", "gamma", "assemble_A", "assemble_sigma_lesser",
+    "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
+    "interface_current", "density", "solve_energy",
+]
+
+
+def _H(x):
+    """Conjugate transpose of the last two axes."""
+    return np.conj(np.swapaxes(x, -1, -2))
+
+
+# ---------------------------------------------------------------------------
+# block-tridiagonal bookkeeping (Sec. II: BT shape of A and B)
+# ---------------------------------------------------------------------------
+
+def dense_matrix(diag, up, low=None):
+    """Dense N x N matrix from BT blocks; lower blocks default to up^H."""
+    nb, b = diag.shape[0], diag.shape[1]
+    M = np.zeros((nb * b, nb * b), dtype=np.complex128)
+    for i in range(nb):
+        M[i * b:(i + 1) * b, i * b:(i + 1) * b] = diag[i]
+    for i in range(nb - 1):
+        M[i * b:(i + 1) * b, (i + 1) * b:(i + 2) * b] = up[i]
+        M[(i + 1) * b:(i + 2) * b, i * b:(i + 1) * b] = _H(up[i]) if low is None else low[i]
+    return M
+
+
+def dense_H_S(dev):
+    """Dense Hamiltonian and overlap (S = I when the device has none)."""
+    H = dense_matrix(dev.H_diag, dev.H_up)
+    if dev.S_diag is None:
+        S = np.eye(H.shape[0], dtype=np.complex128)
+    else:
+        S = dense_matrix(dev.S_diag, dev.S_up)
+    return H, S
+
+
+def _blk(M, i, j, b):
+    return M[i * b:(i + 1) * b, j * b:(j + 1) * b]
+
+
+# ---------------------------------------------------------------------------
+# open boundary conditions (Sec. II "LSE+OBC"; decimation of Lopez Sancho et al.)
+# ---------------------------------------------------------------------------
+
+def lead_A_blocks(dev, side, z):
+    """A-form blocks of a semi-infinite lead, A = z S - H.
+
+    The left lead repeats block 0 with cell-to-cell hop H_{0,1}; the right lead
+    repeats block nb-1 with hop H_{nb-2,nb-1}.  Returns (a00, a01, a10) with
+    a01 the coupling from a cell to the next cell on its right and a10 the
+    coupling back: a01 = z S01 - H01, a10 = z S01^H - H01^H."""
+    b = dev.b
+    if side == "L":
+        H00, H01 = dev.H_diag[0], dev.H_up[0]
+        S00 = np.eye(b) if dev.S_diag is None else dev.S_diag[0]
+        S01 = np.zeros((b, b)) if dev.S_up is None else dev.S_up[0]
+    else:
+        H00, H01 = dev.H_diag[-1], dev.H_up[-1]
+        S00 = np.eye(b) if dev.S_diag is None else dev.S_diag[-1]
+        S01 = np.zeros((b, b)) if dev.S_up is None else dev.S_up[-1]
+    a00 = z * S00 - H00
+    a01 = z * S01 - H01
+    a10 = z * _H(S01) - _H(H01)
+    return a00, a01, a10
+
+
+def sancho_rubio(a00, alpha, beta, tol=1e-12, max_iter=100):
+    """Surface Green's function of a semi-infinite chain by decimation.
+
+    The chain has onsite A-block ``a00`` on every cell, coupling ``alpha`` from
+    a cell to the next one away from the surface and ``beta`` back.  Each step
+    eliminates every other cell (a Schur complement), doubling the reach of the
+    effective couplings:
+        g = eps^{-1};  eps_s -= alpha g beta;  eps -= alpha g beta + beta g alpha;
+        alpha <- -alpha g alpha;  beta <- -beta g beta,
+    until max|alpha|, max|beta| fall below ``tol`` times their initial size.
+    Returns (g_surface = eps_s^{-1}, iterations, converged)."""
+    eps = a00.copy()
+    eps_s = a00.copy()
+    al = alpha.copy()
+    be = beta.copy()
+    ref = max(np.abs(alpha).max(), np.abs(beta).max(), 1e-300)
+    it = 0
+    converged = False
+    while it < max_iter:
+        if max(np.abs(al).max(), np.abs(be).max()) < tol * ref:
+            converged = True
+            break
+        g = np.linalg.inv(eps)
+        agb = al @ g @ be
+        bga = be @ g @ al
+        eps_s = eps_s - agb
+        eps = eps - agb - bga
+        al = -(al @ g @ al)
+        be = -(be @ g @ be)
+        it += 1
+    if not converged and max(np.abs(al).max(), np.abs(be).max()) < tol * ref:
+        converged = True
+    return np.linalg.inv(eps_s), it, converged
+
+
+def surface_residual(a00, alpha, beta, g):
+    """|| (a00 - alpha g beta) g - I ||_F / sqrt(b): how far g is from the
+    fixed point g = (a00 - alpha g beta)^{-1} of the semi-infinite chain."""
+    b = a00.shape[0]
+    R = (a00 - alpha @ g @ beta) @ g - np.eye(b)
+    return np.linalg.norm(R) / np.sqrt(b)
+
+
+def stein_smith(P, Q, C, tol=1e-15, max_iter=200):
+    """Solve D = C + P D Q by Smith's doubling: D = sum_k P^k C Q^k, summed
+    as S <- S + P_j S Q_j, P_{j+1} = P_j^2, Q_{j+1} = Q_j^2."""
+    S = C.copy()
+    Pj = P.copy()
+    Qj = Q.copy()
+    for _ in range(max_iter):
+        inc = Pj @ S @ Qj
+        S = S + inc
+        if np.abs(inc).max() <= tol * max(np.abs(S).max(), 1e-300):
+            break
+        Pj = Pj @ Pj
+        Qj = Qj @ Qj
+        # only the products P_j (.) Q_j matter: keep the two factors balanced so
+        # that neither overflows while the other underflows (rho(P) rho(Q) ~ 1)
+        p, q = np.abs(Pj).max(), np.abs(Qj).max()
+        if p > 0 and q > 0:
+            s = np.sqrt(q / p)
+            Pj *= s
+            Qj /= s
+    return S
+
+
+def surface_newton(a00, alpha, beta, g, target=1e-13, max_steps=3):
+    """Newton steps on F(X) = (a00 - alpha X beta) X - I = 0 starting at ``g``.
+
+    With K = a00 - alpha X beta the step D solves K D - alpha D beta X = -F,
+    i.e. the Stein equation D = -K^{-1} F + (K^{-1} alpha) D (beta X).
+    Returns (X, steps taken, final residual)."""
+    X = g
+    res = surface_residual(a00, alpha, beta, X)
+    steps = 0
+    b = a00.shape[0]
+    while res > target and steps < max_steps:
+        K = a00 - alpha @ X @ beta
+        F = K @ X - np.eye(b)
+        Kinv = np.linalg.inv(K)
+        D = stein_smith(Kinv @ alpha, beta @ X, -(Kinv @ F))
+        Xn = X + D
+        rn = surface_residual(a00, alpha, beta, Xn)
+        steps += 1
+        if not rn < res:
+            break
+        X, res = Xn, rn
+    return X, steps, res
+
+
+def surface_gf(a00, alpha, beta, tol=1e-12, max_iter=100, target=1e-13, newton_steps=3):
+    """Surface Green's function: decimation, then Newton polishing of the
+    fixed-point equation when rounding in the decimation (ill-conditioned
+    intermediate eps near band edges at small eta) left a residual above
+    ``target``.  Returns (g, decimation iterations, newton steps, residual, converged)."""
+    g, it, ok = sancho_rubio(a00, alpha, beta, tol, max_iter)
+    g, ns, res = surface_newton(a00, alpha, beta, g, target, newton_steps)
+    return g, it, ns, res, ok
+
+
+def lead_self_energies(dev, z, tol=1e-12, max_iter=100, newton_steps=3):
+    """Retarded lead self-energies on blocks 0 and nb-1.
+
+    Right lead (cells nb, nb+1, ...): surface g_R from (a00, a01, a10) and
+    Sigma_R = a01 g_R a10.  Left lead (cells -1, -2, ...): couplings swapped,
+    Sigma_L = a10 g_L a01.  Returns (Sigma_L, Sigma_R, info)."""
+    a00, a01, a10 = lead_A_blocks(dev, "L", z)
+    gL, itL, nL, resL, okL = surface_gf(a00, a10, a01, tol, max_iter, newton_steps=newton_steps)
+    sL = a10 @ gL @ a01
+    a00, a01, a10 = lead_A_blocks(dev, "R", z)
+    gR, itR, nR, resR, okR = surface_gf(a00, a01, a10, tol, max_iter, newton_steps=newton_steps)
+    sR = a01 @ gR @ a10
+    info = dict(iters=(itL, itR), newton=(nL, nR), converged=(okL, okR),
+                residual=(resL, resR), g=(gL, gR))
+    return sL, sR, info
+
+
+def gamma(sigma):
+    """Broadening Gamma = i (Sigma^R - Sigma^A)."""
+    return 1j * (sigma - _H(sigma))
+
+
+def lead_lesser(sigma, f):
+    """Lead lesser self-energy Sigma^< = i f Gamma."""
+    return 1j * f * gamma(sigma)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (1) and Eq. (2) by dense inversion
+# ---------------------------------------------------------------------------
+
+def assemble_A(dev, z, sigma_L, sigma_R, sigR_scat=None):
+    """Dense A(z) = z S - H - Sigma^R_OBC - Sigma^R_scat (Eq. (1) operand)."""
+    H, S = dense_H_S(dev)
+    b, nb = dev.b, dev.nb
+    A = z * S - H
+    _blk(A, 0, 0, b)[...] -= sigma_L
+    _blk(A, nb - 1, nb - 1, b)[...] -= sigma_R
+    if sigR_scat is not None:
+        for i in range(nb):
+            _blk(A, i, i, b)[...] -= sigR_scat[i]
+    return A
+
+
+def assemble_sigma_lesser(dev, sigma_L, sigma_R, fL, fR, sigL_scat=None):
+    """Dense block-diagonal Sigma^< = Sigma^<_scat + i f_L Gamma_L (block 0)
+    + i f_R Gamma_R (block nb-1)  (the B^< of Eq. (2))."""
+    b, nb = dev.b, dev.nb
+    N = nb * b
+    SL = np.zeros((N, N), dtype=np.complex128)
+    _blk(SL, 0, 0, b)[...] += lead_lesser(sigma_L, fL)
+    _blk(SL, nb - 1, nb - 1, b)[...] += lead_lesser(sigma_R, fR)
+    if sigL_scat is not None:
+        for i in range(nb):
+            _blk(SL, i, i, b)[...] += sigL_scat[i]
+    return SL
+
+
+def greens_dense(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_scat=None,
+                 keep_dense=False):
+    """Selected blocks of G^R (Eq. (1)) and, when occupations are given, of
+    G^< = G^R Sigma^< G^A (Eq. (2)), by inverting the full matrix.
+
+    Returns a dict with GR_diag [nb], GR_up [nb-1] (block (i,i+1)),
+    GR_low [nb-1] (block (i+1,i)), and GL_diag, GL_low likewise."""
+    b, nb = dev.b, dev.nb
+    A = assemble_A(dev, z, sigma_L, sigma_R, sigR_scat)
+    G = np.linalg.inv(A)
+    out = dict(
+        GR_diag=np.stack([_blk(G, i, i, b) for i in range(nb)]),
+        GR_up=np.stack([_blk(G, i, i + 1, b) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, b, b), complex),
+        GR_low=np.stack([_blk(G, i + 1, i, b) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, b, b), complex),
+        GR_corner=_blk(G, 0, nb - 1, b).copy(),
+    )
+    if fL is not None:
+        SL = assemble_sigma_lesser(dev, sigma_L, sigma_R, fL, fR, sigL_scat)
+        GL = G @ SL @ _H(G)
+        out["GL_diag"] = np.stack([_blk(GL, i, i, b) for i in range(nb)])
+        out["GL_low"] = (np.stack([_blk(GL, i + 1, i, b) for i in range(nb - 1)])
+                         if nb > 1 else np.zeros((0, b, b), complex))
+        out["GL_up"] = (np.stack([_blk(GL, i, i + 1, b) for i in range(nb - 1)])
+                        if nb > 1 else np.zeros((0, b, b), complex))
+        if keep_dense:
+            out["GL"] = GL
+            out["SigmaL"] = SL
+    if keep_dense:
+        out["G"] = G
+        out["A"] = A
+    return out
+
+
+# ---------------------------------------------------------------------------
+# textbook RGF (the recursion the paper cites in Sec. II), plain block loop
+# ---------------------------------------------------------------------------
+
+def _A_blocks(dev, z, sigma_L, sigma_R, sigR_scat=None):
+    nb, b = dev.nb, dev.b
+    S_d = [np.eye(b)] * nb if dev.S_diag is None else list(dev.S_diag)
+    S_u = [np.zeros((b, b))] * (nb - 1) if dev.S_up is None else list(dev.S_up)
+    Ad = [z * S_d[i] - dev.H_diag[i] for i in range(nb)]
+    Ad[0] = Ad[0] - sigma_L
+    Ad[nb - 1] = Ad[nb - 1] - sigma_R
+    if sigR_scat is not None:
+        Ad = [Ad[i] - sigR_scat[i] for i in range(nb)]
+    Au = [z * S_u[i] - dev.H_up[i] for i in range(nb - 1)]           # A_{i,i+1}
+    Al = [z * _H(S_u[i]) - _H(dev.H_up[i]) for i in range(nb - 1)]   # A_{i+1,i}
+    return Ad, Au, Al
+
+
+def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_scat=None):
+    """Selected blocks of G^R and G^< by the forward/backward block recursion.
+
+    Forward:  g_0 = A_00^{-1},  g_i = (A_ii - A_{i,i-1} g_{i-1} A_{i-1,i})^{-1};
+              g^<_i = g_i (Sigma^<_ii + A_{i,i-1} g^<_{i-1} A_{i,i-1}^H) g_i^H.
+    Backward: G_{nb-1} = g_{nb-1};  with X = g_i A_{i,i+1}, Y = A_{i+1,i} g_i:
+              G_{i,i+1} = -X G_{i+1,i+1},  G_{i+1,i} = -G_{i+1,i+1} Y,
+              G_ii = g_i - G_{i,i+1} Y;
+              with Z = A_{i+1,i} g^<_i, P = G^<_{i+1,i+1} X^H:
+              G^<_ii = g^<_i + X P - G_{i,i+1} Z + (G_{i,i+1} Z)^H,
+              G^<_{i+1,i} = -G_{i+1,i+1} Z - P."""
+    nb = dev.nb
+    Ad, Au, Al = _A_blocks(dev, z, sigma_L, sigma_R, sigR_scat)
+    inv = np.linalg.inv
+    g = [None] * nb
+    g[0] = inv(Ad[0])
+    for i in range(1, nb):
+        g[i] = inv(Ad[i] - Al[i - 1] @ g[i - 1] @ Au[i - 1])
+    GR_d = [None] * nb
+    GR_u = [None] * (nb - 1)
+    GR_l = [None] * (nb - 1)
+    GR_d[nb - 1] = g[nb - 1]
+    for i in range(nb - 2, -1, -1):
+        X = g[i] @ Au[i]
+        Y = Al[i] @ g[i]
+        GR_u[i] = -X @ GR_d[i + 1]
+        GR_l[i] = -GR_d[i + 1] @ Y
+        GR_d[i] = g[i] - GR_u[i] @ Y
+    out = dict(GR_diag=np.stack(GR_d))
+    b = dev.b
+    out["GR_up"] = np.stack(GR_u) if nb > 1 else np.zeros((0, b, b), complex)
+    out["GR_low"] = np.stack(GR_l) if nb > 1 else np.zeros((0, b, b), complex)
+    if fL is None:
+        return out
+    SigL = [np.zeros((b, b), complex) for _ in range(nb)]
+    SigL[0] = SigL[0] + lead_lesser(sigma_L, fL)
+    SigL[nb - 1] = SigL[nb - 1] + lead_lesser(sigma_R, fR)
+    if sigL_scat is not None:
+        SigL = [SigL[i] + sigL_scat[i] for i in range(nb)]
+    gl = [None] * nb
+    gl[0] = g[0] @ SigL[0] @ _H(g[0])
+    for i in range(1, nb):
+        gl[i] = g[i] @ (SigL[i] + Al[i - 1] @ gl[i - 1] @ _H(Al[i - 1])) @ _H(g[i])
+    GL_d = [None] * nb
+    GL_l = [None] * (nb - 1)
+    GL_d[nb - 1] = gl[nb - 1]
+    for i in range(nb - 2, -1, -1):
+        X = g[i] @ Au[i]
+        Z = Al[i] @ gl[i]
+        P = GL_d[i + 1] @ _H(X)
+        W = GR_u[i] @ Z
+        GL_d[i] = gl[i] + X @ P - W + _H(W)
+        GL_l[i] = -GR_d[i + 1] @ Z - P
+    out["GL_diag"] = np.stack(GL_d)
+    out["GL_low"] = np.stack(GL_l) if nb > 1 else np.zeros((0, b, b), complex)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# observables (Sec. III: DOS, spectral current and its conservation, density)
+# ---------------------------------------------------------------------------
+
+def transmission_caroli(sigma_L, sigma_R, G_corner):
+    """Ballistic T(E) = Tr[Gamma_L G_{0,nb-1} Gamma_R G_{0,nb-1}^H]."""
+    return float(np.real(np.trace(gamma(sigma_L) @ G_corner @ gamma(sigma_R) @ _H(G_corner))))
+
+
+def transmission_g00(sigma_L, G00):
+    """T from the first diagonal block only:
+    Tr[Gamma_L i(G_00 - G_00^H)] - Tr[Gamma_L G_00 Gamma_L G_00^H]
+    (equal to the Caroli form up to O(eta ||G||^2))."""
+    GL = gamma(sigma_L)
+    t = np.trace(GL @ (1j * (G00 - _H(G00)))) - np.trace(GL @ G00 @ GL @ _H(G00))
+    return float(np.real(t))
+
+
+def dos(dev, GR_diag, GR_up, GR_low):
+    """DOS(E) = -(1/pi) Im Tr[G^R S], summed over the BT pattern of S."""
+    nb = dev.nb
+    if dev.S_diag is None:
+        tr = sum(np.trace(GR_diag[i]) for i in range(nb))
+    else:
+        tr = sum(np.trace(GR_diag[i] @ dev.S_diag[i]) for i in range(nb))
+        for i in range(nb - 1):
+            tr += np.trace(GR_up[i] @ _H(dev.S_up[i]))   # G_{i,i+1} S_{i+1,i}
+            tr += np.trace(GR_low[i] @ dev.S_up[i])      # G_{i+1,i} S_{i,i+1}
+    return float(-np.imag(tr) / np.pi)
+
+
+def interface_current(dev, z, GL_low):
+    """Spectral current through each interface i | i+1:
+    J_i(E) = 2 Re Tr[(H_{i,i+1} - z S_{i,i+1}) G^<_{i+1,i}]  (length nb-1)."""
+    nb, b = dev.nb, dev.b
+    J = np.zeros(max(nb - 1, 0))
+    for i in range(nb - 1):
+        Su = np.zeros((b, b)) if dev.S_up is None else dev.S_up[i]
+        J[i] = 2.0 * np.real(np.trace((dev.H_up[i] - z * Su) @ GL_low[i]))
+    return J
+
+
+def density_energy(dev, GL_diag, GL_low):
+    """Per-energy orbital occupation -i diag(G^< S) / (2 pi) over the BT pattern
+    (real part), length N = nb * b."""
+    nb, b = dev.nb, dev.b
+    out = np.zeros(nb * b)
+    for i in range(nb):
+        if dev.S_diag is None:
+            d = np.diag(GL_diag[i])
+        else:
+            M = GL_diag[i] @ dev.S_diag[i]
+            if i + 1 < nb:   # G^<_{i,i+1} S_{i+1,i},  G^<_{i,i+1} = -(G^<_{i+1,i})^H
+                M = M + (-_H(GL_low[i])) @ _H(dev.S_up[i])
+            if i > 0:        # G^<_{i,i-1} S_{i-1,i}
+                M = M + GL_low[i - 1] @ dev.S_up[i - 1]
+            d = np.diag(M)
+        out[i * b:(i + 1) * b] = np.real(-1j * d) / (2.0 * np.pi)
+    return out
+
+
+def density(dev, weights, GL_diag_E, GL_low_E):
+    """Energy-integrated density n_k = sum_E w_E (-i)(G^< S)_kk(E) / (2 pi)."""
+    n = np.zeros(dev.nb * dev.b)
+    for e in range(len(weights)):
+        n += weights[e] * density_energy(dev, GL_diag_E[e], GL_low_E[e])
+    return n
+
+
+# ---------------------------------------------------------------------------
+# one energy, end to end
+# ---------------------------------------------------------------------------
+
+def solve_energy(dev, e, *, lesser=True, use_rgf=False, tol=1e-12, max_iter=100,
+                 sigma=None):
+    """OBC + Eq. (1)/(2) + observables for energy index ``e`` of ``dev``."""
+    z = dev.energy[e] + 1j * dev.eta
+    if sigma is None:
+        sL, sR, info = lead_self_energies(dev, z, tol, max_iter)
+    else:
+        sL, sR = sigma
+        info = {}
+    fL = dev.f_L()[e] if lesser else None
+    fR = dev.f_R()[e] if lesser else None
+    sR_scat = dev.sigR_scat
+    sL_scat = None
+    if lesser and dev.sigL_base is not None:
+        sL_scat = dev.sigL_scale[e][:, None, None] * dev.sigL_base
+    if use_rgf:
+        out = rgf_blocks(dev, z, sL, sR, fL, fR, sR_scat, sL_scat)
+    else:
+        out = greens_dense(dev, z, sL, sR, fL, fR, sR_scat, sL_scat)
+        out["T_caroli"] = transmission_caroli(sL, sR, out["GR_corner"])
+    out["sigma_L"], out["sigma_R"], out["obc"] = sL, sR, info
+    out["T"] = transmission_g00(sL, out["GR_diag"][0])
+    out["dos"] = dos(dev, out["GR_diag"], out["GR_up"], out["GR_low"])
+    if lesser:
+        out["J"] = interface_current(dev, z, out["GL_low"])
+        out["n_E"] = density_energy(dev, out["GL_diag"], out["GL_low"])
+    return out

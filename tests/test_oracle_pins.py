@@ -1,0 +1,358 @@
+"""Pins of the CPU oracle against closed forms, invariants and brute force.
+
+Each test ties an oracle function to something other than itself: a closed
+form (1D chain surface function, integer transmission of a perfect wire), an
+independent library routine (generalized eigendecomposition), brute force (a
+long finite chain inverted densely), or an exact identity of Eqs. (1)-(2)
+(anti-Hermiticity of G^<, the spectral identity, current continuity).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as W
+from oracle import negf_oracle as O
+
+H = lambda x: np.conj(np.swapaxes(x, -1, -2))
+
+
+# --- OBC: closed form of the 1D chain ------------------------------------------
+
+def chain_surface_closed_form(E, t, eta):
+    """g = (z - sqrt(z^2 - 4t^2)) / (2 t^2), branch with |g t| <= 1 (retarded)."""
+    z = E + 1j * eta
+    r = np.sqrt(z * z - 4 * t * t + 0j)
+    g1 = (z - r) / (2 * t * t)
+    g2 = (z + r) / (2 * t * t)
+    return g1 if abs(g1 * t) <= abs(g2 * t) else g2
+
+
+@pytest.mark.parametrize("t", [1.0, 0.7])
+@pytest.mark.parametrize("E", [-2.5, -1.9, -1.0, -0.3, 0.0, 0.45, 1.3, 1.99, 2.01, 3.0])
+def test_chain_surface_closed_form(E, t):
+    eta = 1e-6
+    z = E + 1j * eta
+    a00 = np.array([[z]])
+    a01 = np.array([[-t + 0j]])
+    g, it, ns, res, ok = O.surface_gf(a00, a01, a01, 1e-12, 100)
+    ref = chain_surface_closed_form(E, t, eta)
+    assert ok
+    assert res <= 1e-10
+    assert abs(g[0, 0] - ref) <= 1e-9 * max(1.0, abs(ref))
+    if abs(E) < 2 * t:
+        assert g[0, 0].imag < 0      # retarded branch in the band
+
+
+# --- OBC + assembly: brute force by a long finite chain ------------------------
+
+def _embedded_device(dev, L):
+    """The device with L explicit lead cells on each side (dense H, S)."""
+    nb, b = dev.nb, dev.b
+    Sd = [np.eye(b)] * nb if dev.S_diag is None else list(dev.S_diag)
+    Su = [np.zeros((b, b))] * (nb - 1) if dev.S_up is None else list(dev.S_up)
+    diag = [dev.H_diag[0]] * L + list(dev.H_diag) + [dev.H_diag[-1]] * L
+    up = [dev.H_up[0]] * L + list(dev.H_up) + [dev.H_up[-1]] * L
+    sdiag = [Sd[0]] * L + Sd + [Sd[-1]] * L
+    sup = [Su[0]] * L + Su + [Su[-1]] * L
+    return (O.dense_matrix(np.array(diag), np.array(up)),
+            O.dense_matrix(np.array(sdiag), np.array(sup)))
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_obc_against_long_finite_chain(overlap):
+    """With eta = 0.05 a chain of 500 explicit lead cells is indistinguishable
+    (e^{-eta L / v}) from the semi-infinite one: the device blocks of its dense
+    inverse must equal the OBC + device solution."""
+    b, nb, L = 3, 4, 500
+    dev = W.banded_device(nb, b, 3, seed=11, overlap=overlap)
+    # make leads strongly coupled (a narrow band lead would hide index mistakes)
+    rng = np.random.default_rng(5)
+    dev.H_up = dev.H_up + 0.4 * (rng.normal(size=dev.H_up.shape) + 1j * rng.normal(size=dev.H_up.shape))
+    dev.eta = 0.05
+    Hbig, Sbig = _embedded_device(dev, L)
+    for E in [-0.7, 0.05, 0.6]:
+        z = E + 1j * dev.eta
+        Gbig = np.linalg.inv(z * Sbig - Hbig)
+        sL, sR, info = O.lead_self_energies(dev, z)
+        out = O.greens_dense(dev, z, sL, sR)
+        off = L * b
+        for i in range(nb):
+            ref = Gbig[off + i * b: off + (i + 1) * b, off + i * b: off + (i + 1) * b]
+            assert np.abs(out["GR_diag"][i] - ref).max() <= 1e-9 * np.abs(ref).max()
+        for i in range(nb - 1):
+            ref_u = Gbig[off + i * b: off + (i + 1) * b, off + (i + 1) * b: off + (i + 2) * b]
+            ref_l = Gbig[off + (i + 1) * b: off + (i + 2) * b, off + i * b: off + (i + 1) * b]
+            assert np.abs(out["GR_up"][i] - ref_u).max() <= 1e-9 * np.abs(ref_u).max()
+            assert np.abs(out["GR_low"][i] - ref_l).max() <= 1e-9 * np.abs(ref_l).max()
+
+
+def test_stein_doubling_against_kronecker():
+    rng = np.random.default_rng(3)
+    n = 5
+    P = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    Q = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    # Smith's series converges for rho(P) rho(Q) < 1; make it slow (0.97)
+    P *= 0.97 / np.abs(np.linalg.eigvals(P)).max()
+    Q /= np.abs(np.linalg.eigvals(Q)).max()
+    P *= 1e3      # badly balanced factors: only the products matter
+    Q *= 1e-3
+    C = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    D = O.stein_smith(P, Q, C)
+    # vec(P D Q) = (Q^T kron P) vec(D) (column-major vec)
+    M = np.eye(n * n) - np.kron(Q.T, P)
+    ref = np.linalg.solve(M, C.reshape(-1, order="F")).reshape(n, n, order="F")
+    assert np.abs(D - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_obc_residual_config1_all_energies():
+    dev = W.config1()
+    for e in range(dev.ne):
+        z = dev.energy[e] + 1j * dev.eta
+        _, _, info = O.lead_self_energies(dev, z)
+        assert all(info["converged"])
+        assert max(info["residual"]) <= 1e-10
+        # Gamma = i(Sigma - Sigma^H) is positive semidefinite for a retarded lead
+    for e in [10, 30, 50]:
+        z = dev.energy[e] + 1j * dev.eta
+        sL, sR, _ = O.lead_self_energies(dev, z)
+        for s in (sL, sR):
+            assert np.linalg.eigvalsh(O.gamma(s)).min() >= -1e-10
+
+
+# --- transmission: integer in the band of a perfect wire -----------------------
+
+def test_ideal_chain_transmission():
+    E = np.array([-2.5, -1.9, -1.2, -0.4, 0.0, 0.7, 1.5, 1.95, 2.05, 2.8])
+    dev = W.ideal_chain(6, 1.0, E)
+    for e in range(dev.ne):
+        out = O.solve_energy(dev, e, lesser=False)
+        expect = 1.0 if abs(E[e]) < 2.0 else 0.0
+        # O(eta N / v) absorption inside the device at eta = 1e-6
+        assert abs(out["T_caroli"] - expect) <= 1e-4
+        assert abs(out["T"] - expect) <= 1e-4
+
+
+def test_ideal_multiorbital_integer_transmission():
+    """A perfect wire of identical cells transmits an integer number of
+    channels; a transposed or mis-signed self-energy breaks this."""
+    H00, H01 = W.config5_lead(0, b=4)
+    E = np.linspace(-3.0, 3.0, 41)
+    dev = W.ideal_multiorbital(5, H00, H01, E)
+    vals = []
+    for e in range(dev.ne):
+        out = O.solve_energy(dev, e, lesser=False)
+        vals.append(out["T_caroli"])
+        # band edges excluded: the O(eta) rounding there is not integer
+        assert abs(out["T_caroli"] - round(out["T_caroli"])) <= 2e-3
+    assert max(vals) >= 2.0 - 1e-3    # several channels open somewhere
+
+
+# --- Eq. (1): dense inverse vs a generalized eigendecomposition ---------------
+
+def test_closed_system_against_eigendecomposition():
+    dev = W.banded_device(3, 4, 5, seed=2)
+    Hd, Sd = O.dense_H_S(dev)
+    lam, V = sla.eigh(Hd, Sd)               # V^H S V = I
+    zero = np.zeros((4, 4), complex)
+    for e in range(dev.ne):
+        z = dev.energy[e] + 0.03j
+        out = O.greens_dense(dev, z, zero, zero, keep_dense=True)
+        Gref = (V / (z - lam)) @ H(V)
+        assert np.abs(out["G"] - Gref).max() <= 1e-11 * np.abs(Gref).max()
+        d_ref = float(-np.imag(np.sum(1.0 / (z - lam))) / np.pi)
+        d = O.dos(dev, out["GR_diag"], out["GR_up"], out["GR_low"])
+        assert abs(d - d_ref) <= 1e-10 * abs(d_ref)
+
+
+# --- RGF recursion vs the definition -------------------------------------------
+
+@pytest.mark.parametrize("nb,b,overlap,scat", [(1, 3, False, False), (2, 3, True, False),
+                                               (5, 4, True, True), (7, 2, False, True)])
+def test_rgf_blocks_equal_dense(nb, b, overlap, scat):
+    if scat:
+        dev = W.small_scattering_device(nb, b, 6, seed=7, overlap=overlap, strength=0.05)
+    else:
+        dev = W.banded_device(nb, b, 6, seed=7, overlap=overlap)
+        rng = np.random.default_rng(1)
+        if nb > 1:
+            dev.H_up = dev.H_up + 0.3 * (rng.normal(size=dev.H_up.shape) + 1j * rng.normal(size=dev.H_up.shape))
+    rng = np.random.default_rng(nb)
+    for e in range(dev.ne):
+        sigma = None
+        if nb == 1:   # no inter-block hop to build leads from: random retarded Sigmas
+            q = rng.normal(size=(2, b, b)) + 1j * rng.normal(size=(2, b, b))
+            sigma = tuple(0.1 * (x + H(x)) - 0.2j * (x @ H(x)) for x in q)
+        a = O.solve_energy(dev, e, sigma=sigma)
+        r = O.solve_energy(dev, e, use_rgf=True, sigma=(a["sigma_L"], a["sigma_R"]))
+        for k in ["GR_diag", "GR_up", "GR_low", "GL_diag", "GL_low"]:
+            if a[k].size == 0:
+                continue
+            scale = np.abs(a[k]).max()
+            assert np.abs(a[k] - r[k]).max() <= 1e-10 * scale, k
+
+
+# --- Eq. (2) invariants -----------------------------------------------------------
+
+def _full_lesser_setup(seed=9):
+    dev = W.small_scattering_device(5, 3, 4, seed=seed, overlap=True, strength=0.05)
+    e = 2
+    z = dev.energy[e] + 1j * dev.eta
+    sL, sR, _ = O.lead_self_energies(dev, z)
+    fL, fR = dev.f_L()[e], dev.f_R()[e]
+    sLs = dev.sigL_scale[e][:, None, None] * dev.sigL_base
+    out = O.greens_dense(dev, z, sL, sR, fL, fR, dev.sigR_scat, sLs, keep_dense=True)
+    return dev, z, sL, sR, fL, fR, sLs, out
+
+
+def test_lesser_is_antihermitian():
+    dev, z, sL, sR, fL, fR, sLs, out = _full_lesser_setup()
+    GL = out["GL"]
+    assert np.abs(GL + H(GL)).max() <= 1e-13 * np.abs(GL).max()
+    for i in range(dev.nb - 1):
+        assert np.abs(out["GL_up"][i] + H(out["GL_low"][i])).max() <= 1e-13 * np.abs(GL).max()
+
+
+def _sigma_greater_dense(dev, sL, sR, fL, fR, sLs):
+    """Sigma^> = Sigma^< + Sigma^R - Sigma^A, block-diagonal."""
+    b, nb = dev.b, dev.nb
+    N = nb * b
+    SR = np.zeros((N, N), complex)
+    SR[:b, :b] += sL
+    SR[-b:, -b:] += sR
+    for i in range(nb):
+        SR[i * b:(i + 1) * b, i * b:(i + 1) * b] += dev.sigR_scat[i]
+    SLs = O.assemble_sigma_lesser(dev, sL, sR, fL, fR, sLs)
+    return SLs + SR - H(SR), SLs
+
+
+def test_spectral_identity_with_eta_term():
+    """i(G^R - G^A) = i(G^> - G^<) + 2 eta G^R S G^A, with G^> = G^R Sigma^> G^A."""
+    dev, z, sL, sR, fL, fR, sLs, out = _full_lesser_setup()
+    G = out["G"]
+    _, S = O.dense_H_S(dev)
+    Sg, SLs = _sigma_greater_dense(dev, sL, sR, fL, fR, sLs)
+    Gg = G @ Sg @ H(G)
+    lhs = 1j * (G - H(G))
+    rhs = 1j * (Gg - out["GL"]) + 2 * dev.eta * G @ S @ H(G)
+    assert np.abs(lhs - rhs).max() <= 1e-10 * np.abs(lhs).max()
+    # without the eta term the identity is off by O(eta ||G||^2) only
+    assert np.abs(lhs - 1j * (Gg - out["GL"])).max() <= 1e3 * dev.eta * np.abs(G).max() ** 2
+
+
+def _continuity_source(dev, i, Sg, SLs, GLd, Ggd, G, S):
+    """Right-hand side of the exact block-i continuity equation of Eq. (2):
+    J_{i-1} - J_i = Tr[Sigma^> G^< - Sigma^< G^>]_ii
+                    + 2i eta Tr[Sigma^<_ii (G S G^A)_ii] - 2i eta Tr[S_ii G^<_ii]
+                    + 4 eta Im Tr[S_{i-1,i} G^<_{i,i-1}]."""
+    b = dev.b
+    s = slice(i * b, (i + 1) * b)
+    sm = slice((i - 1) * b, i * b)
+    GSGA = G @ S @ H(G)
+    src = np.trace(Sg[s, s] @ GLd[s, s] - SLs[s, s] @ Ggd[s, s])
+    src += 2j * dev.eta * np.trace(SLs[s, s] @ GSGA[s, s])
+    src -= 2j * dev.eta * np.trace(S[s, s] @ GLd[s, s])
+    src += 4 * dev.eta * np.imag(np.trace(S[sm, s] @ GLd[s, sm]))
+    return src
+
+
+def test_current_continuity_with_scattering():
+    """Current is conserved block by block up to the scattering source and the
+    eta sink (exact identity); with random scattering J_i varies along x."""
+    dev, z, sL, sR, fL, fR, sLs, out = _full_lesser_setup()
+    G = out["G"]
+    _, S = O.dense_H_S(dev)
+    Sg, SLs = _sigma_greater_dense(dev, sL, sR, fL, fR, sLs)
+    Gg = G @ Sg @ H(G)
+    J = O.interface_current(dev, z, out["GL_low"])
+    scale = np.abs(J).max()
+    for i in range(1, dev.nb - 1):
+        src = _continuity_source(dev, i, Sg, SLs, out["GL"], Gg, G, S)
+        assert abs(src.imag) <= 1e-9 * scale
+        assert abs((J[i - 1] - J[i]) - src.real) <= 1e-9 * scale
+    assert np.ptp(J) > 1e-4 * scale
+
+
+def test_ballistic_current_conservation():
+    """Ballistic: J_{i-1} - J_i is the eta sink alone (exact), and J_i equals
+    T (f_L - f_R) up to O(eta ||G||^2) (the Sec. III conservation check)."""
+    dev = W.config1()
+    nb, b = dev.nb, dev.b
+    _, S = O.dense_H_S(dev)
+    for e in [21, 31, 33, 40, 44]:
+        z = dev.energy[e] + 1j * dev.eta
+        sL, sR, _ = O.lead_self_energies(dev, z)
+        fL, fR = dev.f_L()[e], dev.f_R()[e]
+        out = O.greens_dense(dev, z, sL, sR, fL, fR, keep_dense=True)
+        G = out["G"]
+        dev.sigR_scat = np.zeros((nb, b, b), complex)
+        Sg, SLs = _sigma_greater_dense(dev, sL, sR, fL, fR, None)
+        dev.sigR_scat = None
+        Gg = G @ Sg @ H(G)
+        J = O.interface_current(dev, z, out["GL_low"])
+        scale = max(np.abs(J).max(), 1e-300)
+        for i in range(1, nb - 1):
+            src = _continuity_source(dev, i, Sg, SLs, out["GL"], Gg, G, S)
+            assert abs((J[i - 1] - J[i]) - src.real) <= 1e-9 * scale
+        if fL - fR > 0.1:
+            Tc = O.transmission_caroli(sL, sR, out["GR_corner"])
+            assert np.abs(J - Tc * (fL - fR)).max() <= 1e-3 * Tc * (fL - fR) + 1e-8
+
+
+def test_transmission_g00_identity():
+    """T_g00 - T_caroli = 2 eta Tr[Gamma_L (G S G^H)_00] exactly (ballistic)."""
+    dev = W.config1()
+    for e in [20, 31, 40, 55]:
+        z = dev.energy[e] + 1j * dev.eta
+        sL, sR, _ = O.lead_self_energies(dev, z)
+        out = O.greens_dense(dev, z, sL, sR, keep_dense=True)
+        G = out["G"]
+        b = dev.b
+        Tc = O.transmission_caroli(sL, sR, out["GR_corner"])
+        Tg = O.transmission_g00(sL, out["GR_diag"][0])
+        corr = 2 * dev.eta * np.real(np.trace(O.gamma(sL) @ (G @ H(G))[:b, :b]))
+        assert abs(Tg - Tc - corr) <= 1e-9 * max(1.0, abs(Tc))
+
+
+def test_equilibrium_density_is_occupied_spectral_function():
+    """f_L = f_R = f:  -i G^< = f [ i(G - G^A) - 2 eta G S G^A ]  (Eq. (2) with
+    Sigma^< = i f Gamma), so the density is the occupied spectral weight."""
+    dev = W.banded_device(4, 3, 7, seed=4, overlap=True)
+    dev.mu_L = dev.mu_R = 0.0
+    rng = np.random.default_rng(2)
+    dev.H_up = dev.H_up + 0.3 * (rng.normal(size=dev.H_up.shape) + 1j * rng.normal(size=dev.H_up.shape))
+    _, S = O.dense_H_S(dev)
+    for e in range(dev.ne):
+        z = dev.energy[e] + 1j * dev.eta
+        sL, sR, _ = O.lead_self_energies(dev, z)
+        f = dev.f_L()[e]
+        out = O.greens_dense(dev, z, sL, sR, f, f, keep_dense=True)
+        G = out["G"]
+        ref = f * (1j * (G - H(G)) - 2 * dev.eta * G @ S @ H(G))
+        assert np.abs(-1j * out["GL"] - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300) + 1e-14
+        # per-orbital density from blocks equals the dense diag(-i G^< S)/2pi
+        nE = O.density_energy(dev, out["GL_diag"], out["GL_low"])
+        dref = np.real(np.diag(-1j * out["GL"] @ S)) / (2 * np.pi)
+        assert np.abs(nE - dref).max() <= 1e-12 * max(np.abs(dref).max(), 1e-300) + 1e-15
+
+
+# --- input generators -----------------------------------------------------------
+
+def test_generators_hermitian_and_positive_overlap():
+    dev = W.config2(nb=4, b=16, ne=4)
+    Hd, Sd = O.dense_H_S(dev)
+    assert np.abs(Hd - H(Hd)).max() == 0.0
+    assert np.linalg.eigvalsh(Sd).min() > 0.5
+    c1 = W.config1()
+    assert c1.H_diag.shape == (16, 8, 8) and c1.ne == 64
+    assert c1.energy[0] == -3.0 and c1.energy[-1] == 3.0
+    a, b2 = W.config1(), W.config1()
+    assert np.array_equal(a.H_up, b2.H_up)
+
+
+def test_config4_scattering_signs():
+    dev = W.small_scattering_device(3, 6, 5, seed=1)
+    for i in range(dev.nb):
+        # Im Sigma^R <= 0  <=>  i(Sigma^R - Sigma^A) >= 0
+        assert np.linalg.eigvalsh(1j * (dev.sigR_scat[i] - H(dev.sigR_scat[i]))).min() >= -1e-14
+        sl = dev.sigL_base[i]
+        assert np.abs(sl + H(sl)).max() <= 1e-15     # Sigma^< anti-Hermitian
