@@ -1,0 +1,177 @@
+/*
+ * negf.h -- C ABI of the GB300 (sm_103a) batched RGF library (libnegf.so).
+ *
+ * The library computes, for many energy points at once, the selected blocks of
+ * the retarded and lesser Green's functions of a block-tridiagonal (BT) system
+ * (paper Sec. II and Eqs. (1)-(2)):
+ *
+ *     G^R(E) = (z S - H - Sigma^R_L - Sigma^R_R - Sigma^R_scat)^{-1},  z = E + i eta   (Eq. (1))
+ *     G^<(E) = G^R Sigma^< G^A,  Sigma^< = Sigma^<_scat + i f_L Gamma_L + i f_R Gamma_R  (Eq. (2))
+ *
+ * returning only the blocks on the BT pattern (Sec. II: "only selected entries
+ * of C are needed"), the lead (open boundary) self-energies, and the
+ * transmission, DOS, interface current and density that follow from them.
+ * Every energy is independent (Sec. II); energies are the batch axis.
+ *
+ * Conventions (all calls):
+ *  - Complex matrices are interleaved (re, im) double precision, row-major,
+ *    layout-compatible with contiguous torch.complex128 / numpy complex128.
+ *  - "device" means GPU global memory.  Every pointer is a device pointer
+ *    owned by the caller unless the comment says "host".  The library owns
+ *    only the workspace of its context.
+ *  - All compute calls are asynchronous on the given CUDA stream (0 = legacy
+ *    default stream).  A negative return means that nothing was enqueued
+ *    (argument error) or that a launch failed; the message is available from
+ *    negf_last_error().  Numerical trouble (no convergence, a singular block)
+ *    is reported per energy in the caller's `status` array (device int32),
+ *    and as the worst code by negf_ctx_sync().
+ *  - Several independent BT devices ("ndev" > 1, the uneven batch) are packed
+ *    device after device.  Offsets are exclusive prefix sums computed by the
+ *    library; negf_layout() returns them so callers can address the packing.
+ *
+ * Per-device packing (b = bs[d], nb = nb[d], ne = ne[d]):
+ *    H_diag, S_diag       : nb     blocks b x b             (device order)
+ *    H_up,   S_up         : nb-1   blocks, block (i, i+1);  block (i+1, i) = (block (i,i+1))^H
+ *    energy, f_L, f_R     : ne     doubles
+ *    sigma_L, sigma_R     : ne     blocks (lead self-energy on block 0 / block nb-1)
+ *    GR_diag, GL_diag     : ne*nb  blocks, energy-major: [e][i]
+ *    GR_up, GR_low, GL_low: ne*(nb-1) blocks, [e][i]: (i,i+1), (i+1,i), (i+1,i)
+ *    current              : ne*(nb-1) doubles,  density: nb*b doubles
+ * G^<_{i,i+1} = -(G^<_{i+1,i})^H is not stored.
+ */
+#ifndef NEGF_H
+#define NEGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct negf_ctx negf_ctx;
+typedef void* negf_stream;   /* a cudaStream_t */
+
+typedef enum {
+  NEGF_OK = 0,
+  NEGF_ERR_ARG = -1,       /* invalid argument; nothing enqueued                     */
+  NEGF_ERR_CUDA = -2,      /* a CUDA runtime call or launch failed                    */
+  NEGF_ERR_NOMEM = -3,     /* workspace too small for even one energy                 */
+  NEGF_ERR_NOCONV = -4,    /* per energy: OBC did not reach its residual target       */
+  NEGF_ERR_SINGULAR = -5,  /* per energy: an exactly zero pivot in a block inverse    */
+  NEGF_ERR_TIMEOUT = -6    /* a device-side wait ran out of its iteration budget      */
+} negf_status;
+
+typedef enum {
+  NEGF_FP64 = 0,   /* every product, inverse and reduction in FP64                        */
+  NEGF_MIXED = 1   /* block GEMMs as 3-term TF32 splits on tcgen05 tensor cores (FP32
+                      accumulate in TMEM); block inverses in FP32 + refinement with an
+                      FP64 residual; inputs/outputs stay complex128                        */
+} negf_precision;
+
+/* One or several independent BT devices. Host struct; device pointers inside. */
+typedef struct {
+  int32_t ndev;              /* number of devices (>= 1)                                 */
+  const int32_t* nb;         /* host [ndev]: blocks per device (>= 1)                    */
+  const int32_t* bs;         /* host [ndev]: block size (1..512)                         */
+  const int32_t* ne;         /* host [ndev]: energies per device (>= 0)                  */
+  const void* H_diag;        /* device, packed as above                                  */
+  const void* H_up;          /* device, packed; may be NULL only if every nb == 1        */
+  const void* S_diag;        /* device or NULL (S = identity)                            */
+  const void* S_up;          /* device or NULL (zero off-diagonal overlap)               */
+  const double* energy;      /* device [sum ne]: real part of z                          */
+  double eta;                /* z = E + i*eta, eta > 0                                    */
+} negf_system;
+
+/* Block-diagonal scattering self-energies (optional; pass NULL for ballistic). */
+typedef struct {
+  const void* sigR;          /* retarded, or NULL                                        */
+  const void* sigL;          /* lesser (anti-Hermitian), or NULL                         */
+  const double* sigL_scale;  /* device [sum ne*nb] factor s[e][i] on sigL, or NULL (= 1)  */
+  int32_t per_energy;        /* 0: [sum nb] blocks shared by all energies of a device;
+                                1: [sum ne*nb] blocks, energy-major                        */
+} negf_scattering;
+
+/* Context: binds a CUDA device and owns `workspace_bytes` of device scratch
+ * (energies are processed in chunks that fit it).  Returns NEGF_ERR_ARG for a
+ * NULL out-pointer, NEGF_ERR_CUDA if the device cannot be used. */
+negf_status negf_ctx_create(negf_ctx** ctx, int device, size_t workspace_bytes);
+negf_status negf_ctx_destroy(negf_ctx* ctx);
+/* Message of the last error raised on this context (never NULL). */
+const char* negf_last_error(const negf_ctx* ctx);
+/* Synchronizes `stream` and returns the worst status raised by device code since
+ * the previous sync (NEGF_ERR_TIMEOUT from a device wait, NEGF_ERR_CUDA for a
+ * failed kernel), then clears it. */
+negf_status negf_ctx_sync(negf_ctx* ctx, negf_stream stream);
+
+/* Host-only integer layout of a (possibly uneven) batch.  Writes, per device d,
+ * 8 int64 to out[8*d .. 8*d+7]:
+ *   [0] diag-block offset   (sum_{d'<d} nb*b*b)        elements into H_diag / S_diag
+ *   [1] up-block offset     (sum_{d'<d} (nb-1)*b*b)    into H_up / S_up
+ *   [2] energy offset       (sum_{d'<d} ne)            into energy / f / status
+ *   [3] lead-block offset   (sum_{d'<d} ne*b*b)        into sigma_L / sigma_R
+ *   [4] G diag offset       (sum_{d'<d} ne*nb*b*b)     into GR_diag / GL_diag
+ *   [5] G off-diag offset   (sum_{d'<d} ne*(nb-1)*b*b) into GR_up / GR_low / GL_low
+ *   [6] current offset      (sum_{d'<d} ne*(nb-1))     into current
+ *   [7] orbital offset      (sum_{d'<d} nb*b)          into density
+ * plus, at out[8*ndev .. 8*ndev+7], the totals.  `out` has 8*(ndev+1) entries. */
+negf_status negf_layout(const negf_system* sys, int64_t* out);
+
+/* Lead self-energies (open boundary term of B^R, Sec. II "LSE+OBC").
+ * The left lead repeats block 0 with hop H_{0,1} (S likewise); the right lead
+ * repeats block nb-1 with hop H_{nb-2,nb-1}.  Surface Green's functions by
+ * Lopez Sancho-Rubio decimation in FP64 (stop when max|alpha|,|beta| < tol *
+ * initial, at most max_iter steps), followed when needed by up to 3 FP64
+ * Newton steps on the surface fixed-point equation; an energy whose surface
+ * residual ||(a00 - a01 g a10) g - I||_F / sqrt(b) stays above 1e-10 gets
+ * NEGF_ERR_NOCONV in status[e].  Sigma_L = a10 g_L a01, Sigma_R = a01 g_R a10.
+ *   g0_L, g0_R : reserved for a warm start, must be NULL.
+ *   sigma_L/R  : out, device [sum ne] blocks.
+ *   iters      : out, device int32 [2*sum ne]: decimation steps (L, R) per energy, or NULL.
+ *   status     : out, device int32 [sum ne] (NEGF_OK or a negative code), or NULL.
+ * Requires nb >= 2 for every device. */
+negf_status negf_obc(negf_ctx* ctx, const negf_system* sys, double tol, int32_t max_iter,
+                     const void* g0_L, const void* g0_R, void* sigma_L, void* sigma_R,
+                     int32_t* iters, int32_t* status, negf_stream stream);
+
+/* Selected blocks of G^R (Eq. (1)) by the forward/backward recursive Green's
+ * function sweeps (RGF, Sec. II).  sigma_L/R from negf_obc (or any retarded
+ * self-energy), scat may be NULL.  GR_diag / GR_up / GR_low: out, each may be
+ * NULL (not returned).  status: device int32 [sum ne] or NULL. */
+negf_status negf_rgf_retarded(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
+                              const void* sigma_L, const void* sigma_R,
+                              const negf_scattering* scat,
+                              void* GR_diag, void* GR_up, void* GR_low,
+                              int32_t* status, negf_stream stream);
+
+/* G^R and G^< = G^R Sigma^< G^A (Eq. (2)) in one fused forward/backward sweep
+ * pair.  f_L, f_R: device [sum ne] lead occupations (Sigma^<_lead = i f Gamma,
+ * Gamma = i (Sigma^R - Sigma^A)).  Outputs as above plus GL_diag, GL_low (each
+ * may be NULL). */
+negf_status negf_rgf_lesser(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
+                            const void* sigma_L, const void* sigma_R,
+                            const double* f_L, const double* f_R,
+                            const negf_scattering* scat,
+                            void* GR_diag, void* GR_up, void* GR_low,
+                            void* GL_diag, void* GL_low,
+                            int32_t* status, negf_stream stream);
+
+/* Observables, FP64 (Sec. III: DOS, spectral current, current conservation):
+ *   T[e]      = Tr[Gamma_L i(G_00 - G_00^H)] - Tr[Gamma_L G_00 Gamma_L G_00^H]     (needs GR_diag)
+ *   dos[e]    = -(1/pi) Im Tr[G^R S] over the BT pattern                          (needs GR_diag,
+ *               and GR_up, GR_low when S_up != NULL)
+ *   current[e][i] = 2 Re Tr[(H_{i,i+1} - z S_{i,i+1}) G^<_{i+1,i}]                 (needs GL_low)
+ *   density[k] = sum_e w[e] Re(-i (G^< S)_kk) / (2 pi)                          (needs GL_diag,
+ *               GL_low when S_up != NULL; e_weight device [sum ne])
+ * Each output may be NULL (skipped).  T: [sum ne], dos: [sum ne]. */
+negf_status negf_observables(negf_ctx* ctx, const negf_system* sys,
+                             const void* sigma_L, const double* e_weight,
+                             const void* GR_diag, const void* GR_up, const void* GR_low,
+                             const void* GL_diag, const void* GL_low,
+                             double* T, double* dos, double* current, double* density,
+                             negf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEGF_H */

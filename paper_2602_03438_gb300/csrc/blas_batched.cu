@@ -1,0 +1,272 @@
+// Batched complex block kernels on CUDA cores: FP64 GEMM and Gauss-Jordan
+// inversion (FP64 or FP32 arithmetic).  These are the building blocks of the
+// RGF recursions (every step is a product or an inverse of b x b blocks,
+// batched over independent energy points, Sec. II of the paper).
+#include "negf_internal.cuh"
+
+namespace negf {
+
+// ---------------------------------------------------------------------------
+// FP64 complex GEMM: D = alpha op(A) op(B) + beta C, one grid z-slice per unit.
+// Output tile TM x TM, 256 threads, (TM/16)^2 outputs per thread, K chunks of 16
+// staged through shared memory.  GB300 runs FP64 at ~1/60 of its FP32 rate, so
+// this kernel is bound by the FP64 pipe, not by memory.
+// ---------------------------------------------------------------------------
+template <int TM>
+__global__ void __launch_bounds__(256) zgemm_f64_kernel(GemmArgs g) {
+  const int u = blockIdx.z;
+  if (g.active && !g.active[u]) return;
+  constexpr int KC = 16;
+  constexpr int R = TM / 16;
+  __shared__ zc As[KC][TM + 1];
+  __shared__ zc Bs[KC][TM + 1];
+  const int n = g.n;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TM;
+  const zc* A = g.A.at(u);
+  const zc* B = g.B.at(u);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  zc acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = zmake(0.0, 0.0);
+
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    for (int idx = threadIdx.x; idx < TM * KC; idx += 256) {
+      int mm, kk;
+      if (g.opA == OP_N) { kk = idx % KC; mm = idx / KC; }
+      else { mm = idx % TM; kk = idx / TM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      zc v = zmake(0.0, 0.0);
+      if (gm < n && gk < n) v = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+      As[kk][mm] = v;
+    }
+    for (int idx = threadIdx.x; idx < TM * KC; idx += 256) {
+      int nn, kk;
+      if (g.opB == OP_N) { nn = idx % TM; kk = idx / TM; }
+      else { kk = idx % KC; nn = idx / KC; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      zc v = zmake(0.0, 0.0);
+      if (gn < n && gk < n) v = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      zc a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) zfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  zc* D = g.D.at(u);
+  const zc* C = g.C.p ? g.C.at(u) : nullptr;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= n) continue;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= n) continue;
+      zc v = zmul(g.alpha, acc[i][j]);
+      if (C) v = zadd(v, zmul(g.beta, C[(size_t)gm * n + gn]));
+      D[(size_t)gm * n + gn] = v;
+    }
+  }
+}
+
+cudaError_t zgemm_f64(const GemmArgs& g, cudaStream_t s) {
+  if (g.units <= 0 || g.n <= 0) return cudaSuccess;
+  if (g.n <= 32) {
+    dim3 grid((g.n + 31) / 32, (g.n + 31) / 32, g.units);
+    zgemm_f64_kernel<32><<<grid, 256, 0, s>>>(g);
+  } else {
+    dim3 grid((g.n + 63) / 64, (g.n + 63) / 64, g.units);
+    zgemm_f64_kernel<64><<<grid, 256, 0, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inversion with partial pivoting, one CTA per unit.
+//   for k: p = first argmax_{r>=k} |W[r][k]|; swap rows p,k; d = W[k][k];
+//          row k <- row k / d with W[k][k] := 1/d;
+//          for r != k: f = W[r][k]; row r <- row r - f * row k with W[r][k] := -f/d
+//   finally undo the row swaps as column swaps in reverse order.
+// ---------------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<double> { typedef double2 T; };
+template <> struct CT<float> { typedef float2 T; };
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T cmk(R a, R b) {
+  typename CT<R>::T v; v.x = a; v.y = b; return v;
+}
+
+constexpr int kInvThreads = 512;
+
+template <typename R, bool SMEM>
+__global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n, const int* active,
+                                                           typename CT<R>::T* scratch, int32_t* status) {
+  typedef typename CT<R>::T C;
+  const int u = blockIdx.x;
+  if (active && !active[u]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* W;
+  unsigned char* tail;
+  if (SMEM) {
+    W = reinterpret_cast<C*>(smem_raw);
+    tail = smem_raw + sizeof(C) * (size_t)n * n;
+  } else {
+    W = scratch + (size_t)u * n * n;
+    tail = smem_raw;
+  }
+  C* prow = reinterpret_cast<C*>(tail);
+  C* fcol = prow + n;
+  int* piv = reinterpret_cast<int*>(fcol + n);
+  __shared__ R red_v[kInvThreads / 32];
+  __shared__ int red_i[kInvThreads / 32];
+  __shared__ int s_p;
+  __shared__ int s_sing;
+
+  const int tid = threadIdx.x;
+  const zc* Min = M.at(u);
+  const int nn = n * n;
+  for (int i = tid; i < nn; i += kInvThreads) {
+    zc v = Min[i];
+    W[i] = cmk<R>((R)v.x, (R)v.y);
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+
+  for (int k = 0; k < n; ++k) {
+    // -- pivot: first row r >= k with the largest |W[r][k]|^2
+    R best = (R)-1;
+    int bi = n;
+    for (int r = k + tid; r < n; r += kInvThreads) {
+      C v = W[(size_t)r * n + k];
+      R a = v.x * v.x + v.y * v.y;
+      if (a > best) { best = a; bi = r; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      R ob = __shfl_down_sync(0xffffffffu, best, off);
+      int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid < 32) {
+      best = (tid < kInvThreads / 32) ? red_v[tid] : (R)-1;
+      bi = (tid < kInvThreads / 32) ? red_i[tid] : n;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        R ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        if (!(best > (R)0)) { s_sing = 1; bi = k; }
+        s_p = bi;
+        piv[k] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    // -- swap rows p and k
+    if (p != k) {
+      for (int c = tid; c < n; c += kInvThreads) {
+        C t = W[(size_t)k * n + c];
+        W[(size_t)k * n + c] = W[(size_t)p * n + c];
+        W[(size_t)p * n + c] = t;
+      }
+      __syncthreads();
+    }
+    // -- scaled pivot row and elimination factors
+    C d = W[(size_t)k * n + k];
+    R den = d.x * d.x + d.y * d.y;
+    C dinv = (den > (R)0) ? cmk<R>(d.x / den, -d.y / den) : cmk<R>((R)0, (R)0);
+    for (int c = tid; c < n; c += kInvThreads) {
+      C v = (c == k) ? cmk<R>((R)1, (R)0) : W[(size_t)k * n + c];
+      prow[c] = cmk<R>(v.x * dinv.x - v.y * dinv.y, v.x * dinv.y + v.y * dinv.x);
+    }
+    for (int r = tid; r < n; r += kInvThreads) fcol[r] = (r == k) ? cmk<R>((R)0, (R)0) : W[(size_t)r * n + k];
+    __syncthreads();
+    // -- rank-1 update of every row (row k becomes the scaled pivot row)
+    for (int i = tid; i < nn; i += kInvThreads) {
+      const int r = i / n, c = i - r * n;
+      if (r == k) {
+        W[i] = prow[c];
+      } else {
+        C w = (c == k) ? cmk<R>((R)0, (R)0) : W[i];
+        C f = fcol[r];
+        C pr = prow[c];
+        w.x = w.x - (f.x * pr.x - f.y * pr.y);
+        w.y = w.y - (f.x * pr.y + f.y * pr.x);
+        W[i] = w;
+      }
+    }
+    __syncthreads();
+  }
+  // -- undo the row interchanges: swap columns k and piv[k], last pivot first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k) {
+      for (int r = tid; r < n; r += kInvThreads) {
+        C t = W[(size_t)r * n + k];
+        W[(size_t)r * n + k] = W[(size_t)r * n + p];
+        W[(size_t)r * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+  zc* Xo = X.at(u);
+  for (int i = tid; i < nn; i += kInvThreads) {
+    C v = W[i];
+    Xo[i] = zmake((double)v.x, (double)v.y);
+  }
+  if (tid == 0 && s_sing && status) status[u] = NEGF_ERR_SINGULAR;
+}
+
+static size_t inv_tail_bytes(int n, size_t csz) { return 2 * csz * n + sizeof(int) * n + 16; }
+static const size_t kInvSmemMax = 200 * 1024;
+
+size_t zinv_scratch_bytes(int n, int units, int single) {
+  const size_t csz = single ? sizeof(float2) : sizeof(double2);
+  if (csz * (size_t)n * n + inv_tail_bytes(n, csz) <= kInvSmemMax) return 0;
+  return csz * (size_t)n * n * units;
+}
+
+template <typename R>
+static cudaError_t launch_inv(BMat X, BMat M, int n, int units, const int* active, void* scratch,
+                              int32_t* status, cudaStream_t s) {
+  typedef typename CT<R>::T C;
+  const size_t full = sizeof(C) * (size_t)n * n + inv_tail_bytes(n, sizeof(C));
+  if (full <= kInvSmemMax) {
+    cudaError_t e = cudaFuncSetAttribute(zinv_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)full);
+    if (e != cudaSuccess) return e;
+    zinv_kernel<R, true><<<units, kInvThreads, full, s>>>(X, M, n, active, nullptr, status);
+  } else {
+    if (!scratch) return cudaErrorInvalidValue;
+    const size_t t = inv_tail_bytes(n, sizeof(C));
+    zinv_kernel<R, false><<<units, kInvThreads, t, s>>>(X, M, n, active, (C*)scratch, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t zinv(BMat X, BMat M, int n, int units, const int* active, int single, void* scratch,
+                 int32_t* status, cudaStream_t s) {
+  if (units <= 0 || n <= 0) return cudaSuccess;
+  if (single) return launch_inv<float>(X, M, n, units, active, scratch, status, s);
+  return launch_inv<double>(X, M, n, units, active, scratch, status, s);
+}
+
+}  // namespace negf

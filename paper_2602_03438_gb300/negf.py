@@ -1,0 +1,294 @@
+"""ctypes binding of libnegf (include/negf.h): argument marshalling only.
+
+Every arithmetic step of the path runs in the CUDA kernels of libnegf.so; this
+module converts torch tensors to raw device pointers and back.  It refuses to
+run without the compiled library (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libnegf.so")
+
+NEGF_OK = 0
+NEGF_ERR_ARG = -1
+NEGF_ERR_CUDA = -2
+NEGF_ERR_NOMEM = -3
+NEGF_ERR_NOCONV = -4
+NEGF_ERR_SINGULAR = -5
+NEGF_ERR_TIMEOUT = -6
+FP64 = 0
+MIXED = 1
+
+EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
+           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables"]
+
+
+class NegfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnegf status {code}: {msg}")
+        self.code = code
+
+
+class _System(C.Structure):
+    _fields_ = [("ndev", C.c_int32), ("nb", C.POINTER(C.c_int32)), ("bs", C.POINTER(C.c_int32)),
+                ("ne", C.POINTER(C.c_int32)), ("H_diag", C.c_void_p), ("H_up", C.c_void_p),
+                ("S_diag", C.c_void_p), ("S_up", C.c_void_p), ("energy", C.c_void_p), ("eta", C.c_double)]
+
+
+class _Scattering(C.Structure):
+    _fields_ = [("sigR", C.c_void_p), ("sigL", C.c_void_p), ("sigL_scale", C.c_void_p),
+                ("per_energy", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libnegf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnegf.so not found at {path}: run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    vp, i32, dbl, sz = C.c_void_p, C.c_int32, C.c_double, C.c_size_t
+    lib.negf_ctx_create.argtypes = [C.POINTER(vp), C.c_int, sz]
+    lib.negf_ctx_destroy.argtypes = [vp]
+    lib.negf_last_error.argtypes = [vp]
+    lib.negf_last_error.restype = C.c_char_p
+    lib.negf_ctx_sync.argtypes = [vp, vp]
+    lib.negf_layout.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64)]
+    lib.negf_obc.argtypes = [vp, C.POINTER(_System), dbl, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_rgf_retarded.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, C.POINTER(_Scattering),
+                                      vp, vp, vp, vp, vp]
+    lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
+                                    vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_observables.argtypes = [vp, C.POINTER(_System), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    for name in EXPORTS:
+        if name != "negf_last_error":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libnegf takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libnegf takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A libnegf context bound to one CUDA device with its own workspace."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 1 << 30):
+        self.lib = load_library()
+        self.h = C.c_void_p()
+        st = self.lib.negf_ctx_create(C.byref(self.h), int(device), C.c_size_t(int(workspace_bytes)))
+        if st != NEGF_OK:
+            raise NegfError(st, self.lib.negf_last_error(None).decode())
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.negf_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st):
+        if st != NEGF_OK:
+            raise NegfError(st, self.lib.negf_last_error(self.h).decode())
+
+    def sync(self, stream=None) -> int:
+        """Synchronize the stream; returns the worst device-side status (0 = OK)."""
+        return int(self.lib.negf_ctx_sync(self.h, _stream(stream)))
+
+
+@dataclass
+class System:
+    """Device-resident packed batch of BT devices (the negf_system of the C ABI)."""
+    nb: List[int]
+    bs: List[int]
+    ne: List[int]
+    H_diag: torch.Tensor
+    H_up: torch.Tensor
+    S_diag: Optional[torch.Tensor]
+    S_up: Optional[torch.Tensor]
+    energy: torch.Tensor
+    eta: float
+    _keep: list = field(default_factory=list, repr=False)
+
+    def c(self) -> _System:
+        n = len(self.nb)
+        arrs = [(C.c_int32 * n)(*self.nb), (C.c_int32 * n)(*self.bs), (C.c_int32 * n)(*self.ne)]
+        self._keep = arrs
+        return _System(n, arrs[0], arrs[1], arrs[2], _ptr(self.H_diag), _ptr(self.H_up),
+                       _ptr(self.S_diag), _ptr(self.S_up), _ptr(self.energy), float(self.eta))
+
+    @property
+    def ndev(self):
+        return len(self.nb)
+
+    def layout(self) -> np.ndarray:
+        """Integer offsets of the packing, [ndev+1, 8] (see negf_layout)."""
+        lib = load_library()
+        out = (C.c_int64 * (8 * (self.ndev + 1)))()
+        s = self.c()
+        st = lib.negf_layout(C.byref(s), out)
+        if st != NEGF_OK:
+            raise NegfError(st, lib.negf_last_error(None).decode())
+        return np.frombuffer(out, dtype=np.int64).reshape(self.ndev + 1, 8).copy()
+
+
+def system_layout(nb: Sequence[int], bs: Sequence[int], ne: Sequence[int]) -> np.ndarray:
+    """negf_layout for shapes only (no device memory touched)."""
+    lib = load_library()
+    n = len(nb)
+    arrs = [(C.c_int32 * n)(*nb), (C.c_int32 * n)(*bs), (C.c_int32 * n)(*ne)]
+    s = _System(n, arrs[0], arrs[1], arrs[2], None, None, None, None, None, 1.0)
+    out = (C.c_int64 * (8 * (n + 1)))()
+    st = lib.negf_layout(C.byref(s), out)
+    if st != NEGF_OK:
+        raise NegfError(st, lib.negf_last_error(None).decode())
+    return np.frombuffer(out, dtype=np.int64).reshape(n + 1, 8).copy()
+
+
+def _dev_tensor(a, device, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device)
+
+
+def upload(devices, device="cuda") -> System:
+    """Pack one or several ``workloads.Device`` objects onto the GPU."""
+    if not isinstance(devices, (list, tuple)):
+        devices = [devices]
+    eta = devices[0].eta
+    if any(d.eta != eta for d in devices):
+        raise ValueError("all devices of a batch share eta")
+    flat = lambda xs: np.concatenate([x.reshape(-1) for x in xs]) if xs else np.zeros(0, np.complex128)
+    has_s = [d.S_diag is not None for d in devices]
+    if any(has_s) and not all(has_s):
+        raise ValueError("either every device has an overlap matrix or none")
+    Hd = _dev_tensor(flat([d.H_diag for d in devices]), device)
+    Hu = _dev_tensor(flat([d.H_up for d in devices]), device)
+    Sd = _dev_tensor(flat([d.S_diag for d in devices]), device) if all(has_s) else None
+    Su = _dev_tensor(flat([d.S_up for d in devices]), device) if all(has_s) else None
+    E = _dev_tensor(np.concatenate([d.energy for d in devices]), device)
+    return System([d.nb for d in devices], [d.b for d in devices], [d.ne for d in devices],
+                  Hd, Hu if Hu.numel() else None, Sd, Su, E, eta)
+
+
+class Scattering:
+    """Block-diagonal scattering self-energies (negf_scattering)."""
+
+    def __init__(self, sigR=None, sigL=None, sigL_scale=None, per_energy=False):
+        self.sigR, self.sigL, self.sigL_scale, self.per_energy = sigR, sigL, sigL_scale, per_energy
+
+    def c(self):
+        return _Scattering(_ptr(self.sigR), _ptr(self.sigL), _ptr(self.sigL_scale), 1 if self.per_energy else 0)
+
+    @staticmethod
+    def from_devices(devices, device="cuda"):
+        if not isinstance(devices, (list, tuple)):
+            devices = [devices]
+        if all(d.sigR_scat is None and d.sigL_base is None for d in devices):
+            return None
+        cat = lambda xs: np.concatenate([x.reshape(-1) for x in xs])
+        sR = _dev_tensor(cat([d.sigR_scat for d in devices]), device) if devices[0].sigR_scat is not None else None
+        sL = _dev_tensor(cat([d.sigL_base for d in devices]), device) if devices[0].sigL_base is not None else None
+        sc = (_dev_tensor(cat([d.sigL_scale for d in devices]), device)
+              if devices[0].sigL_scale is not None else None)
+        return Scattering(sR, sL, sc, False)
+
+
+def _scat_ptr(scat):
+    return C.byref(scat.c()) if scat is not None else None
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def negf_obc(ctx: Context, sys: System, sigma_L, sigma_R, iters=None, status=None, tol=1e-12, max_iter=100,
+             stream=None):
+    s = sys.c()
+    ctx.check(ctx.lib.negf_obc(ctx.h, C.byref(s), float(tol), int(max_iter), None, None, _ptr(sigma_L),
+                               _ptr(sigma_R), _ptr(iters), _ptr(status), _stream(stream)))
+
+
+def negf_rgf_retarded(ctx: Context, sys: System, prec, sigma_L, sigma_R, scat=None, GR_diag=None, GR_up=None,
+                      GR_low=None, status=None, stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_retarded(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(sigma_R),
+                                        C.byref(sc) if sc is not None else None, _ptr(GR_diag), _ptr(GR_up),
+                                        _ptr(GR_low), _ptr(status), _stream(stream)))
+
+
+def negf_rgf_lesser(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, scat=None, GR_diag=None,
+                    GR_up=None, GR_low=None, GL_diag=None, GL_low=None, status=None, stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_lesser(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(sigma_R), _ptr(f_L),
+                                      _ptr(f_R), C.byref(sc) if sc is not None else None, _ptr(GR_diag),
+                                      _ptr(GR_up), _ptr(GR_low), _ptr(GL_diag), _ptr(GL_low), _ptr(status),
+                                      _stream(stream)))
+
+
+def negf_observables(ctx: Context, sys: System, sigma_L=None, e_weight=None, GR_diag=None, GR_up=None,
+                     GR_low=None, GL_diag=None, GL_low=None, T=None, dos=None, current=None, density=None,
+                     stream=None):
+    s = sys.c()
+    ctx.check(ctx.lib.negf_observables(ctx.h, C.byref(s), _ptr(sigma_L), _ptr(e_weight), _ptr(GR_diag),
+                                       _ptr(GR_up), _ptr(GR_low), _ptr(GL_diag), _ptr(GL_low), _ptr(T), _ptr(dos),
+                                       _ptr(current), _ptr(density), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# output allocation helper (torch is the allocator)
+# ---------------------------------------------------------------------------
+
+def allocate_outputs(sys: System, lesser=True, device="cuda", want_up_low=True):
+    L = sys.layout()
+    tot = L[-1]
+    z = lambda n: torch.empty(int(n), dtype=torch.complex128, device=device)
+    out = dict(
+        sigma_L=z(tot[3]), sigma_R=z(tot[3]),
+        iters=torch.zeros(2 * int(tot[2]), dtype=torch.int32, device=device),
+        obc_status=torch.zeros(int(tot[2]), dtype=torch.int32, device=device),
+        status=torch.zeros(int(tot[2]), dtype=torch.int32, device=device),
+        GR_diag=z(tot[4]),
+        GR_up=z(tot[5]) if want_up_low else None,
+        GR_low=z(tot[5]) if want_up_low else None,
+        T=torch.zeros(int(tot[2]), dtype=torch.float64, device=device),
+        dos=torch.zeros(int(tot[2]), dtype=torch.float64, device=device),
+    )
+    if lesser:
+        out.update(GL_diag=z(tot[4]), GL_low=z(tot[5]),
+                   current=torch.zeros(int(tot[6]), dtype=torch.float64, device=device),
+                   density=torch.zeros(int(tot[7]), dtype=torch.float64, device=device))
+    return out

@@ -1,0 +1,83 @@
+"""CPU-only checks of the C ABI: the library loads, exports every entry point
+declared in include/negf.h, and its integer batch layout is bit-exact."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "negf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_03438_gb300 import negf
+    if not os.path.exists(negf.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return negf.load_library()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(negf_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ["negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_ctx_create"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2602_03438_gb300 import negf
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(negf.EXPORTS) <= set(declared_functions())
+
+
+def _layout_py(shapes):
+    """Exclusive prefix sums of the packing, recomputed in Python."""
+    acc = [0] * 8
+    rows = []
+    for nb, b, ne in shapes:
+        rows.append(list(acc))
+        bb = b * b
+        inc = [nb * bb, (nb - 1) * bb, ne, ne * bb, ne * nb * bb, ne * (nb - 1) * bb, ne * (nb - 1), nb * b]
+        acc = [a + i for a, i in zip(acc, inc)]
+    rows.append(acc)
+    return np.array(rows, dtype=np.int64)
+
+
+def test_uneven_layout_is_bit_exact(lib):
+    from paper_2602_03438_gb300 import negf
+    shapes = W.config3_shapes()
+    assert len(shapes) == 256
+    got = negf.system_layout([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes])
+    assert np.array_equal(got, _layout_py(shapes))
+    # every (device, energy, block) addressed exactly once
+    tot = got[-1]
+    assert tot[4] == sum(ne * nb * b * b for nb, b, ne in shapes)
+
+
+def test_layout_rejects_bad_shapes(lib):
+    from paper_2602_03438_gb300 import negf
+    with pytest.raises(negf.NegfError) as ei:
+        negf.system_layout([4], [513], [2])
+    assert ei.value.code == negf.NEGF_ERR_ARG
+    with pytest.raises(negf.NegfError):
+        negf.system_layout([0], [8], [2])
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    from paper_2602_03438_gb300 import negf
+    assert lib.negf_obc(None, None, 1e-12, 10, None, None, None, None, None, None, None) == negf.NEGF_ERR_ARG
+    assert lib.negf_rgf_lesser(None, None, 0, None, None, None, None, None, None, None, None, None,
+                               None, None, None) == negf.NEGF_ERR_ARG
+    assert lib.negf_layout(None, None) == negf.NEGF_ERR_ARG
+    assert b"NULL" in lib.negf_last_error(None)
