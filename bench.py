@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Throughput of the batched RGF hot path on GB300.
+
+One step = the whole path over one batch: lead self-energies (OBC), the fused
+G^R + G^< forward/backward sweeps, and the observables (T, DOS, current,
+density), for 1024 energy points of the ballistic nb = 64, b = 128 device
+(S = I + 0.05 R).  ``value`` is energy points per second for the whole job
+(all ranks), inputs resident in HBM; ``e2e`` repeats it through host buffers.
+With torchrun (N > 1) every rank solves its own 1024 energies (weak scaling,
+no data-path collective: energies are independent).
+
+``--impl reference`` times the CPU oracle (numpy complex128) on a bounded
+sample of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = ("energy points/sec (G^R+G^< RGF, nb=64, bs=128) mixed vs FP64 on 1 GB300 at ≤1e-6 rel")
+UNIT = "energy points/s"
+
+
+# ---------------------------------------------------------------------------
+# helpers (host logic; covered by CPU tests)
+# ---------------------------------------------------------------------------
+
+def rank_energies(ne_per_rank, rank, world, e_min=-3.0, e_max=3.0):
+    """Energies of one rank: the global grid of ne_per_rank*world points,
+    interleaved so that every rank sees the same spread of in-band and
+    out-of-band energies."""
+    grid = np.linspace(e_min, e_max, ne_per_rank * world)
+    return grid[rank::world].copy()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def roofline_for(cls, stats, peaks, peak_src, sustained=True):
+    """Roofline object for one kernel class from live event timings.
+
+    gemm_tc : 3-term TF32 split complex GEMM.  achieved = useful complex flops
+              (8 n^3 per product) / time; peak = TF32 dense peak / 3, the TF32
+              peak taken as the bf16 peak x (1.1 / 2.25) (nominal ratio).
+    gemm_f64, inv_f64: FP64 pipe ("alu"), peak 1.25 TFLOP/s nominal.
+    inv_f32 : FP32 CUDA cores ("alu"), peak 152 SM x 128 lanes x 2 x 2.07 GHz."""
+    ms = stats["ms"]
+    fl = stats["flops"]
+    n = max(stats["launches"], 1)
+    per_launch_s = ms / 1e3 / n
+    achieved = (fl / n) / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+    if cls == "gemm_tc":
+        bound, peak, unit = "tensor", bf16 * (1.1 / 2.25) / 3.0, "TFLOP/s"
+        note = f"useful complex flops vs TF32 peak/3 (TF32 = bf16 {peak_src} x 1.1/2.25)"
+    elif cls in ("gemm_f64", "inv_f64"):
+        bound, peak, unit = "alu", 1.25, "TFLOP/s"
+        note = "FP64 pipe, nominal 1.25 TFLOP/s"
+    elif cls == "inv_f32":
+        bound, peak, unit = "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s"
+        note = "FP32 CUDA cores, 152 SM x 128 x 2 x 2.07 GHz"
+    else:
+        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+        achieved = (stats["bytes"] / n) / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+        note = f"HBM ({peak_src})"
+    return {"kernel": cls, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak if peak else None, "launches": stats["launches"],
+            "avg_launch_ms": ms / n, "peak_source": f"{peak_src}: {note}"}
+
+
+def traffic_for(cls):
+    """Per-launch DRAM traffic of the kernel class from the committed ncu summary,
+    or None when that capture does not match the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(cls)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+
+def oracle_step(dev, idx, weights):
+    """The whole path for energies ``idx`` with the CPU oracle: OBC, the block
+    recursion for G^R and G^< (pinned to dense inversion by the tests), T, DOS,
+    current and the weighted density contribution."""
+    from oracle import negf_oracle as O
+    n = np.zeros(dev.nb * dev.b)
+    for e in idx:
+        out = O.solve_energy(dev, int(e), lesser=True, use_rgf=True)
+        n += weights[e] * out["n_E"]
+    return n
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(dev, budget_s=15.0, min_energies=2):
+    """Times the oracle on a bounded, spread-out sample of the workload's energies."""
+    w = dev.weights()
+    order = np.random.default_rng(0).permutation(dev.ne)
+    t0 = time.perf_counter()
+    done = 0
+    for e in order:
+        oracle_step(dev, [e], w)
+        done += 1
+        if done >= min_energies and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{done} of {dev.ne} energies of the nb={dev.nb}, b={dev.b} device "
+                      f"(OBC + block RGF G^R/G^< + observables, numpy complex128), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    dev = W.config2(nb=args.nb, b=args.b, ne=args.ne)
+    w = dev.weights()
+    rng = np.random.default_rng(1)
+    per = args.ref_energies
+    for _ in range(args.warmup):
+        oracle_step(dev, rng.choice(dev.ne, per, replace=False), w)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(dev, rng.choice(dev.ne, per, replace=False), w)
+    dt = time.perf_counter() - t0
+    val = per * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"config 2: ballistic batched RGF, nb={args.nb}, b={args.b}, "
+                                   f"{args.ne} energies in [-3,3], S=I+0.05R; each step {per} sampled energies",
+                       "nb": args.nb, "b": args.b, "energies": args.ne},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{per} random energies per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def rel_block_err(a, b, nblk):
+    """max over blocks of ||a_i - b_i||_F / max over blocks ||b_i||_F, per energy, max over energies."""
+    a = a.reshape(a.shape[0], nblk, -1)
+    b = b.reshape(b.shape[0], nblk, -1)
+    num = np.linalg.norm(a - b, axis=2).max(axis=1)
+    den = np.maximum(np.linalg.norm(b, axis=2).max(axis=1), 1e-300)
+    return float((num / den).max())
+
+
+def run_gpu(args):
+    import torch
+    import paper_2602_03438_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    dev = W.config2(nb=args.nb, b=args.b, ne=args.ne)
+    dev.energy = rank_energies(args.ne, rank, world)
+    prec = P.MIXED if args.prec == "mixed" else P.FP64
+    nb, b, ne = dev.nb, dev.b, dev.ne
+
+    ctx = P.Context(local, int(args.workspace_gb * (1 << 30)))
+    sys_ = P.upload(dev)
+    out = P.allocate_outputs(sys_)
+    fL = torch.from_numpy(dev.f_L()).cuda()
+    fR = torch.from_numpy(dev.f_R()).cuda()
+    w = torch.from_numpy(dev.weights()).cuda()
+    stream = torch.cuda.current_stream()
+
+    def obc():
+        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"])
+
+    def rgf(p=prec, s=sys_, o=out, ffL=fL, ffR=fR):
+        P.negf_rgf_lesser(ctx, s, p, o["sigma_L"], o["sigma_R"], ffL, ffR, None, o["GR_diag"], o["GR_up"],
+                          o["GR_low"], o["GL_diag"], o["GL_low"], o["status"])
+
+    def obs():
+        P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
+                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"])
+
+    def step():
+        obc()
+        rgf()
+        obs()
+
+    for _ in range(args.warmup):
+        step()
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after warm-up")
+    bad_obc = int((out["obc_status"] != 0).sum().item())
+    bad = int((out["status"] != 0).sum().item())
+
+    # ---- timed region: whole path, K steps, kernel events live
+    ctx.profile_reset()
+    ctx.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ctx.profile(False)
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, world, device=torch.device("cuda", local))
+    prof = ctx.profile_read()
+    value = world * ne * args.steps / (ms / 1e3)
+
+    # ---- RGF alone (the metric's own definition: Sigma_OBC precomputed)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rgf()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_rgf = max_over_ranks(ev0.elapsed_time(ev1), world, device=torch.device("cuda", local))
+    rgf_value = world * ne * args.steps / (ms_rgf / 1e3)
+
+    # ---- FP64 comparison on a bounded subset of the energies (same device, same Sigma)
+    cmp = {}
+    if args.fp64_sample > 0 and rank == 0:
+        k = min(args.fp64_sample, ne)
+        idx = np.linspace(0, ne - 1, k).round().astype(int)
+        sub = W.config2(nb=args.nb, b=args.b, ne=args.ne)
+        sub.energy = dev.energy[idx]
+        s2 = P.upload(sub)
+        o2 = P.allocate_outputs(s2)
+        bb = b * b
+        sl = out["sigma_L"].view(ne, bb)[torch.from_numpy(idx).cuda()].reshape(-1)
+        sr = out["sigma_R"].view(ne, bb)[torch.from_numpy(idx).cuda()].reshape(-1)
+        o2["sigma_L"].copy_(sl)
+        o2["sigma_R"].copy_(sr)
+        f2L = fL[torch.from_numpy(idx).cuda()].contiguous()
+        f2R = fR[torch.from_numpy(idx).cuda()].contiguous()
+        rgf(P.FP64, s2, o2, f2L, f2R)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        rgf(P.FP64, s2, o2, f2L, f2R)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        fp64_value = k / (ms64 / 1e3)
+        errs = {}
+        for key, nblk in (("GR_diag", nb), ("GR_up", nb - 1), ("GR_low", nb - 1), ("GL_diag", nb),
+                          ("GL_low", nb - 1)):
+            got = out[key].view(ne, -1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+            ref = o2[key].view(k, -1).cpu().numpy()
+            errs[key] = rel_block_err(got, ref, nblk)
+        cmp = {"fp64_rgf_value": fp64_value, "fp64_energies": k, "speedup_vs_fp64": rgf_value / world / fp64_value,
+               "err_vs_fp64_max": max(errs.values()), "err_vs_fp64": errs}
+        del o2, s2
+
+    # ---- end to end through host buffers: H2D inputs, the path, D2H observables
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.cpu().pin_memory()
+        h_in = {k: pin(getattr(sys_, k)) for k in ("H_diag", "H_up", "S_diag", "S_up", "energy")}
+        h_in.update(fL=pin(fL), fR=pin(fR), w=pin(w))
+        d_in = {k: getattr(sys_, k) for k in ("H_diag", "H_up", "S_diag", "S_up", "energy")}
+        d_in.update(fL=fL, fR=fR, w=w)
+        outs_d2h = ("T", "dos", "current", "density", "status", "obc_status")
+        h_out = {k: torch.empty_like(out[k], device="cpu").pin_memory() for k in outs_d2h}
+        h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+        d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            for kk, t in h_in.items():
+                d_in[kk].copy_(t, non_blocking=True)
+            step()
+            for kk in outs_d2h:
+                h_out[kk].copy_(out[kk], non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms_e2e = max_over_ranks(max(ev0.elapsed_time(ev1), wall * 1e3), world, device=torch.device("cuda", local))
+        e2e = {"value": world * ne * args.steps / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e / args.steps,
+               "result": "T, DOS, current, density and status arrays"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peaks, src = measured_peaks()
+    cls_ms = {k: v["ms"] for k, v in prof["classes"].items() if v["launches"] > 0}
+    dominant = max(cls_ms, key=cls_ms.get)
+    roof = roofline_for(dominant, prof["classes"][dominant], peaks, src, sustained=True)
+    roof["traffic"] = traffic_for(dominant)
+    shares = {k: v / sum(cls_ms.values()) for k, v in cls_ms.items()}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "tf32x3+f32+f64 (mixed)" if prec == P.MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"config 2: ballistic batched RGF, nb={nb}, b={b}, {ne} energies/GPU in [-3,3], "
+                               "S=I+0.05R, eta=1e-6; step = OBC + G^R/G^< sweeps + observables",
+                   "nb": nb, "b": b, "energies_per_gpu": ne, "precision": args.prec,
+                   "parallelism": f"energy-sharded x{world}",
+                   "l2": "working set larger than L2 (85 GB of G blocks written per step)"},
+        "rgf_only": {"value": rgf_value, "unit": UNIT, "ms_per_step": ms_rgf / args.steps},
+        "fp64_comparison": cmp,
+        "status": {"obc_not_converged": bad_obc, "rgf_flagged": bad},
+        "gpu_launches": prof["launches"],
+        "kernel_time_share": shares,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(dev, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nb", type=int, default=64)
+    ap.add_argument("--b", type=int, default=128)
+    ap.add_argument("--ne", type=int, default=1024)
+    ap.add_argument("--workspace-gb", type=float, default=24.0)
+    ap.add_argument("--fp64-sample", type=int, default=64)
+    ap.add_argument("--ref-energies", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,42 @@ negf_status negf_observables(negf_ctx* ctx, const negf_system* sys,
                              double* T, double* dos, double* current, double* density,
                              negf_stream stream);
 
+/* Building blocks of the sweeps, exposed for testing and reuse.
+ *
+ * Batched complex block product (every step of the RGF recursions is one):
+ *   D[u] = alpha op_A(A[u]) op_B(B[u]) + beta C[u],  u = 0..units-1, n x n row-major
+ * complex128 blocks; X[u] lives at X + u * x_stride (elements; 0 = one block shared
+ * by all units).  op: 0 = as stored, 2 = conjugate transpose.  alpha, beta: host
+ * double[2] (re, im).  C may be NULL (beta ignored) or equal to D; D must not
+ * overlap A or B.  NEGF_FP64: FP64 FMA; NEGF_MIXED: 3-term TF32 split on the
+ * tensor cores for n >= 16 (FP64 below). */
+negf_status negf_block_gemm(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, int32_t opA,
+                            int32_t opB, const double* alpha, const void* A, int64_t a_stride, const void* B,
+                            int64_t b_stride, const double* beta, const void* C, int64_t c_stride, void* D,
+                            int64_t d_stride, negf_stream stream);
+/* Batched block inverse X[u] = M[u]^{-1} (unit stride n*n; X may equal M):
+ * Gauss-Jordan with partial pivoting (first largest |.| in row order).
+ * NEGF_FP64: in FP64.  NEGF_MIXED: in FP32, then one refinement step
+ * X <- X + X (I - M X) with the residual formed in FP64.  status (device
+ * int32 [units] or NULL) gets NEGF_ERR_SINGULAR on an exactly zero pivot. */
+negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, const void* M,
+                               void* X, int32_t* status, negf_stream stream);
+
+/* Kernel timing (the tracing facility).  When enabled, every launch of the
+ * block-GEMM and block-inverse kernels is bracketed by CUDA events recorded on
+ * the launch stream; negf_profile_read() synchronizes on those events and
+ * accumulates them.  Not a paper operation: measurement support. */
+negf_status negf_profile_enable(negf_ctx* ctx, int enable);
+/* Accumulated since the last reset: `launches` = all kernels this context has
+ * launched; per kernel class k (0 = tensor-core GEMM, 1 = FP64 GEMM, 2 = FP32
+ * inverse, 3 = FP64 inverse, 4 = other) the launches, total milliseconds,
+ * algorithmic flops (8 n^3 per complex n x n product or inverse, times the
+ * units) and algorithmic bytes (16 n^2 per operand read or written).  Each
+ * array has 5 entries; any pointer may be NULL. */
+negf_status negf_profile_read(negf_ctx* ctx, int64_t* launches, int64_t* k_launches, double* k_ms,
+                              double* k_flops, double* k_bytes);
+negf_status negf_profile_reset(negf_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,9 @@ negf_status fail(Ctx* c, negf_status code, const std::string& msg) {
   return code;
 }
 
+// launch check that also counts the kernel for the context's launch counter
+#define KCHECK() do { ++ctx->launches; CU(cudaGetLastError()); } while (0)
+
 #define CU(call)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -250,20 +253,54 @@ struct Engine {
   cudaStream_t s;
   int mixed;
   void* inv_scratch;   // for inverses too large for shared memory
+  // timing facility: events around one launch of class `cls`
+  int open_cls = -1;
+  cudaEvent_t open_ev = nullptr;
+  void begin(int cls) {
+    ++ctx->launches;
+    if (!ctx->prof) return;
+    open_cls = cls;
+    open_ev = ctx->take_event();
+    cudaEventRecord(open_ev, s);
+  }
+  void end(double flops, double bytes) {
+    if (!ctx->prof || open_cls < 0) return;
+    cudaEvent_t e1 = ctx->take_event();
+    cudaEventRecord(e1, s);
+    ctx->recs.push_back(ProfRec{open_cls, open_ev, e1, flops, bytes});
+    open_cls = -1;
+  }
   cudaError_t gemm(BMat D, BMat A, int opA, BMat B, int opB, zc alpha, BMat C, zc beta, int n, int units,
                    const int* active = nullptr) {
     GemmArgs g;
     g.D = D; g.A = A; g.B = B; g.C = C;
     g.opA = opA; g.opB = opB; g.alpha = alpha; g.beta = beta;
     g.n = n; g.units = units; g.active = active;
-    if (mixed && tc_supported(n)) return zgemm_tc(g, ctx->d_err, s);
-    return zgemm_f64(g, s);
+    const double nn = (double)n * n;
+    const double flops = 8.0 * nn * n * units;                        // useful complex flops
+    const double bytes = 16.0 * nn * units * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
+    cudaError_t e;
+    if (mixed && tc_supported(n)) {
+      begin(K_GEMM_TC);
+      e = zgemm_tc(g, ctx->d_err, s);
+    } else {
+      begin(K_GEMM_F64);
+      e = zgemm_f64(g, s);
+    }
+    end(flops, bytes);
+    return e;
+  }
+  cudaError_t inv(BMat X, BMat M, int n, int units, const int* active, int single, int32_t* status) {
+    begin(single ? K_INV_F32 : K_INV_F64);
+    cudaError_t e = zinv(X, M, n, units, active, single, inv_scratch, status, s);
+    end(8.0 * (double)n * n * n * units, 32.0 * (double)n * n * units);
+    return e;
   }
   // X = M^{-1}.  Mixed precision: FP32 Gauss-Jordan, then `refine` steps of
   // X <- X + X (I - M X) with the residual I - M X formed in FP64 and the
   // correction product on the engine's GEMM.  T1, T2: scratch slots.
   cudaError_t inverse(BMat X, BMat M, int n, int units, int32_t* status, BMat T1, BMat T2, int refine = 1) {
-    cudaError_t e = zinv(X, M, n, units, nullptr, mixed, inv_scratch, status, s);
+    cudaError_t e = inv(X, M, n, units, nullptr, mixed, status);
     if (e != cudaSuccess || !mixed) return e;
     const long long nn = (long long)n * n;
     dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), units);
@@ -272,12 +309,17 @@ struct Engine {
       r.D = T1; r.A = M; r.B = X; r.C = BMat{nullptr, 0};
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
       r.n = n; r.units = units; r.active = nullptr;
-      if ((e = zgemm_f64(r, s)) != cudaSuccess) return e;                  // M X   (FP64)
+      begin(K_GEMM_F64);
+      e = zgemm_f64(r, s);                                                 // M X   (FP64)
+      end(8.0 * (double)n * n * n * units, 48.0 * (double)n * n * units);
+      if (e != cudaSuccess) return e;
+      ++ctx->launches;
       one_minus_kernel<<<grid, 256, 0, s>>>(T1, n);                        // I - M X
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = gemm(T2, X, OP_N, T1, OP_N, zmake(1.0, 0.0), BMat{nullptr, 0}, zmake(0.0, 0.0), n, units)) !=
           cudaSuccess)
         return e;                                                          // X (I - M X)
+      ++ctx->launches;
       add_kernel<<<grid, 256, 0, s>>>(X, X, T2, n, nullptr);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -347,6 +389,7 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     a.Adiag = Adiag; a.SigL = SigL;
     a.Aup = (i > 0) ? Aup : nullptr;
     a.Alow = (i > 0) ? Alow : nullptr;
+    ++ctx->launches;
     CU(assemble(a, s));
     if (i == 0) {
       CU(eng.inverse(gD(0), S1(Adiag), b, U, st, S1(T[1]), S1(T[2])));
@@ -374,6 +417,7 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     a.i_diag = -1;
     a.i_off = i;
     a.Aup = Aup; a.Alow = Alow;
+    ++ctx->launches;
     CU(assemble(a, s));
     const BMat X = S1(T[0]);
     const BMat Gup = io.GRu ? offB(io.GRu, i) : S1(gup_tmp);
@@ -390,6 +434,7 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
       CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U));
       // G^<_ii = g^<_i + X P - W + W^H
       CU(eng.gemm(glD(i), X, OP_N, P, OP_N, ONE, glD(i), ONE, b, U));
+      ++ctx->launches;
       CU(antiherm_update(glD(i), Wm, b, U, s));
       // G^<_{i+1,i} = -G_{i+1,i+1} Z - P
       if (io.GLl) CU(eng.gemm(offB(io.GLl, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U));
@@ -820,6 +865,8 @@ negf_status negf_ctx_destroy(negf_ctx* c) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  for (const ProfRec& r : ctx->recs) { cudaEventDestroy(r.ev0); cudaEventDestroy(r.ev1); }
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
   return NEGF_OK;
 }
@@ -974,45 +1021,46 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       LeadArgs la{dv, e0, U, a00.p, al0.p, be0.p, eps.p, epss.p, al.p, be.p};
       dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), NU);
       lead_init_kernel<<<eg, 256, 0, s>>>(la);
-      CU(cudaGetLastError());
+      KCHECK();
       lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 0, ref, done, act, it_arr, 0, tol, n_active);
-      CU(cudaGetLastError());
+      KCHECK();
       // ---- decimation
       for (int it = 0; it <= max_iter; ++it) {
         const bool poll = (it & 3) == 3 || it == max_iter;
         if (poll) CU(cudaMemsetAsync(n_active, 0, sizeof(int), s));
         lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 1, ref, done, act, it_arr, it, tol,
                                             poll ? n_active : nullptr);
-        CU(cudaGetLastError());
+        KCHECK();
         if (poll) {
           CU(cudaMemcpyAsync(ctx->h_pinned, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
           CU(cudaStreamSynchronize(s));
           if (ctx->h_pinned[0] == 0) break;
         }
         if (it == max_iter) break;
-        CU(zinv(g, eps, b, NU, act, 0, eng.inv_scratch, nullptr, s));                     // g = eps^{-1}
+        CU(eng.inv(g, eps, b, NU, act, 0, nullptr));                     // g = eps^{-1}
         CU(eng.gemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // al g
         CU(eng.gemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // be g
         CU(eng.gemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // al g be
         CU(eng.gemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // be g al
         lead_update_kernel<<<eg, 256, 0, s>>>(eps, epss, T[2], T[3], b, done);
-        CU(cudaGetLastError());
+        KCHECK();
         CU(eng.gemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -al g al
         CU(eng.gemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -be g be
         std::swap(al, T[4]);
         std::swap(be, T[5]);
       }
       // ---- surface function and its residual
-      CU(zinv(g, epss, b, NU, nullptr, 0, eng.inv_scratch, nullptr, s));
+      CU(eng.inv(g, epss, b, NU, nullptr, 0, nullptr));
       auto residual = [&](BMat X, double* out, const int* mask) -> negf_status {
         CU(eng.gemm(T[0], al0, OP_N, X, OP_N, ONE, NOMAT, ZERO, b, NU, mask));               // al X
         CU(eng.gemm(T[1], T[0], OP_N, be0, OP_N, MONE, a00, ONE, b, NU, mask));              // K = a00 - al X be
         CU(eng.gemm(T[2], T[1], OP_N, X, OP_N, ONE, NOMAT, ZERO, b, NU, mask));              // K X
         residual_kernel<<<NU, 256, 0, s>>>(T[2], b, out, mask);                              // F = K X - I
-        CU(cudaGetLastError());
+        KCHECK();
         return NEGF_OK;
       };
       auto n_set = [&](const int* flags) -> int {
+        ++ctx->launches;
         count_kernel<<<1, 256, 0, s>>>(flags, NU, n_active);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -1024,14 +1072,14 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       // K D - al D (be g) = -F, solved as the Stein equation D = -K^{-1}F + (K^{-1} al) D (be g)
       // by Smith doubling, for the units whose residual is above the target
       set_need_kernel<<<(NU + 255) / 256, 256, 0, s>>>(res, need, NU, target);
-      CU(cudaGetLastError());
+      KCHECK();
       BMat gn = eps;   // decimation slots are free now
       for (int step = 0; step < 3; ++step) {
         int cnt = n_set(need);
         if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
         if (cnt == 0) break;
         // T1 = K and T2 = F of the current g (left there by the last residual evaluation)
-        CU(zinv(T[3], T[1], b, NU, need, 0, eng.inv_scratch, nullptr, s));                 // K^{-1}
+        CU(eng.inv(T[3], T[1], b, NU, need, 0, nullptr));                 // K^{-1}
         CU(eng.gemm(T[4], T[3], OP_N, al0, OP_N, ONE, NOMAT, ZERO, b, NU, need));          // P = K^{-1} al
         CU(eng.gemm(T[5], be0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, need));             // Q = be g
         CU(eng.gemm(T[6], T[3], OP_N, T[2], OP_N, MONE, NOMAT, ZERO, b, NU, need));        // S = -K^{-1} F
@@ -1041,13 +1089,13 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
           CU(eng.gemm(W1, Pm, OP_N, Sm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P S
           CU(eng.gemm(W2, W1, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P S Q
           smith_accum_kernel<<<NU, 256, 0, s>>>(Sm, W2, b, act, 1e-15);
-          CU(cudaGetLastError());
+          KCHECK();
           CU(eng.gemm(W1, Pm, OP_N, Pm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P^2
           CU(eng.gemm(W3, Qm, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // Q^2
           std::swap(Pm, W1);
           std::swap(Qm, W3);
           balance_kernel<<<NU, 256, 0, s>>>(Pm, Qm, b, act);
-          CU(cudaGetLastError());
+          KCHECK();
           if ((j & 7) == 7) {
             cnt = n_set(act);
             if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
@@ -1055,10 +1103,10 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
           }
         }
         add_kernel<<<eg, 256, 0, s>>>(gn, g, Sm, b, need);                                  // g + D
-        CU(cudaGetLastError());
+        KCHECK();
         if ((st = residual(gn, resn, need)) != NEGF_OK) return st;
         newton_accept_kernel<<<NU, 256, 0, s>>>(g, gn, b, res, resn, need, target);
-        CU(cudaGetLastError());
+        KCHECK();
         // units that took the step continue from T1/T2 (K, F of the accepted g)
       }
       // sigma = al0 g be0 (left units -> sigma_L, right -> sigma_R)
@@ -1070,7 +1118,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
                   BMat{be0.p + (long long)U * bb, bb}, OP_N, ONE, NOMAT, ZERO, b, U));
       obc_finish_kernel<<<(U + 127) / 128, 128, 0, s>>>(done, res, it_arr, U, status ? status + o[2] + e0 : nullptr,
                                                         iters ? iters + 2 * (o[2] + e0) : nullptr, accept);
-      CU(cudaGetLastError());
+      KCHECK();
     }
   }
   return NEGF_OK;
@@ -1118,33 +1166,124 @@ negf_status negf_observables(negf_ctx* c, const negf_system* sys, const void* si
         BMat G00{(zc*)GR_diag + o[4] + (long long)e0 * nb * bb, (long long)nb * bb};
         dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), U);
         gamma_kernel<<<eg, 256, 0, s>>>(Gam, Sg, b);
-        CU(cudaGetLastError());
+        KCHECK();
         CU(eng.gemm(K1, Gam, OP_N, G00, OP_N, ONE, NOMAT, ZERO, b, U));
         CU(eng.gemm(K2, G00, OP_N, Gam, OP_N, ONE, NOMAT, ZERO, b, U));
         transmission_kernel<<<U, 256, 0, s>>>(Gam, G00, K1, K2, b, T + o[2] + e0);
-        CU(cudaGetLastError());
+        KCHECK();
       }
       if (dos) {
         dos_kernel<<<U, 256, 0, s>>>(dv, (const zc*)GR_diag + o[4], GR_up ? (const zc*)GR_up + o[5] : nullptr,
                                      GR_low ? (const zc*)GR_low + o[5] : nullptr, e0, dos + o[2]);
-        CU(cudaGetLastError());
+        KCHECK();
       }
       if (current && nb > 1) {
         current_kernel<<<dim3(nb - 1, U), 256, 0, s>>>(dv, (const zc*)GL_low + o[5], e0, current + o[6]);
-        CU(cudaGetLastError());
+        KCHECK();
       }
       if (density) {
         double* nE = (double*)ctx->ws;
         dim3 g1((unsigned)std::min<long long>((N + 255) / 256, 1024), U);
         density_energy_kernel<<<g1, 256, 0, s>>>(dv, (const zc*)GL_diag + o[4],
                                                  GL_low ? (const zc*)GL_low + o[5] : nullptr, e0, nE);
-        CU(cudaGetLastError());
+        KCHECK();
         density_accum_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 1024), 256, 0, s>>>(
             nE, e_weight + o[2], e0, U, N, density + o[7]);
-        CU(cudaGetLastError());
+        KCHECK();
       }
     }
   }
+  return NEGF_OK;
+}
+
+negf_status negf_profile_enable(negf_ctx* c, int enable) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  ctx->prof = enable != 0;
+  return NEGF_OK;
+}
+
+negf_status negf_profile_read(negf_ctx* c, int64_t* launches, int64_t* k_launches, double* k_ms, double* k_flops,
+                              double* k_bytes) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  CU(cudaSetDevice(ctx->device));
+  for (const ProfRec& r : ctx->recs) {
+    CU(cudaEventSynchronize(r.ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, r.ev0, r.ev1));
+    ctx->k_launches[r.cls] += 1;
+    ctx->k_ms[r.cls] += ms;
+    ctx->k_flops[r.cls] += r.flops;
+    ctx->k_bytes[r.cls] += r.bytes;
+    ctx->pool.push_back(r.ev0);
+    ctx->pool.push_back(r.ev1);
+  }
+  ctx->recs.clear();
+  if (launches) *launches = ctx->launches;
+  for (int k = 0; k < K_NCLASS; ++k) {
+    if (k_launches) k_launches[k] = ctx->k_launches[k];
+    if (k_ms) k_ms[k] = ctx->k_ms[k];
+    if (k_flops) k_flops[k] = ctx->k_flops[k];
+    if (k_bytes) k_bytes[k] = ctx->k_bytes[k];
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_profile_reset(negf_ctx* c) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  int64_t dummy;
+  negf_status st = negf_profile_read(c, &dummy, nullptr, nullptr, nullptr, nullptr);
+  if (st != NEGF_OK) return st;
+  ctx->launches = 0;
+  for (int k = 0; k < K_NCLASS; ++k) {
+    ctx->k_launches[k] = 0; ctx->k_ms[k] = 0; ctx->k_flops[k] = 0; ctx->k_bytes[k] = 0;
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_block_gemm(negf_ctx* c, negf_precision prec, int32_t n, int32_t units, int32_t opA, int32_t opB,
+                            const double* alpha, const void* A, int64_t a_stride, const void* B, int64_t b_stride,
+                            const double* beta, const void* C, int64_t c_stride, void* D, int64_t d_stride,
+                            negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > 4096 || units < 0 || units > 65535) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 4096, 0 <= units <= 65535");
+  if ((opA != OP_N && opA != OP_H) || (opB != OP_N && opB != OP_H)) return fail(ctx, NEGF_ERR_ARG, "op must be 0 or 2");
+  if (!alpha || !A || !B || !D || (C && !beta)) return fail(ctx, NEGF_ERR_ARG, "NULL operand");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED) return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (a_stride < 0 || b_stride < 0 || c_stride < 0 || d_stride < 0) return fail(ctx, NEGF_ERR_ARG, "negative stride");
+  if (d_stride == 0 && units > 1) return fail(ctx, NEGF_ERR_ARG, "D cannot be shared by several units");
+  CU(cudaSetDevice(ctx->device));
+  Engine eng{ctx, (cudaStream_t)stream, prec == NEGF_MIXED ? 1 : 0, nullptr};
+  CU(eng.gemm(BMat{(zc*)D, d_stride}, BMat{(zc*)A, a_stride}, opA, BMat{(zc*)B, b_stride}, opB,
+              zmake(alpha[0], alpha[1]), C ? BMat{(zc*)C, c_stride} : NOMAT,
+              C ? zmake(beta[0], beta[1]) : ZERO, n, units));
+  return NEGF_OK;
+}
+
+negf_status negf_block_inverse(negf_ctx* c, negf_precision prec, int32_t n, int32_t units, const void* M, void* X,
+                               int32_t* status, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > 512 || units < 0) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 512, units >= 0");
+  if (!M || !X) return fail(ctx, NEGF_ERR_ARG, "NULL operand");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED) return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (units == 0) return NEGF_OK;
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int mixed = prec == NEGF_MIXED ? 1 : 0;
+  const long long bb = (long long)n * n;
+  // workspace: two scratch slots for the refinement, then the inverse scratch
+  const size_t need = (size_t)units * bb * sizeof(zc) * (mixed ? 2 : 0) + zinv_scratch_bytes(n, units, mixed);
+  if (need > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for this batch of inverses");
+  zc* ws = (zc*)ctx->ws;
+  Engine eng{ctx, s, mixed, nullptr};
+  BMat T1{ws, bb}, T2{ws + (mixed ? units * bb : 0), bb};
+  eng.inv_scratch = (void*)(ws + (mixed ? 2 * units * bb : 0));
+  if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * units, s));
+  CU(eng.inverse(BMat{(zc*)X, bb}, BMat{(zc*)M, bb}, n, units, status, T1, T2));
   return NEGF_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/negf.h"
 
@@ -54,6 +55,15 @@ struct GemmArgs {
 // ---------------------------------------------------------------------------
 // library context
 // ---------------------------------------------------------------------------
+// kernel classes of the timing facility (negf_profile_*)
+enum KClass { K_GEMM_TC = 0, K_GEMM_F64 = 1, K_INV_F32 = 2, K_INV_F64 = 3, K_OTHER = 4, K_NCLASS = 5 };
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t ev0, ev1;
+  double flops, bytes;
+};
+
 struct Ctx {
   int device = 0;
   int num_sms = 0;
@@ -62,6 +72,20 @@ struct Ctx {
   int* d_err = nullptr;         // device error word (worst negative code, as min)
   int* h_pinned = nullptr;      // small pinned host buffer for flags
   std::string last_error;
+  long long launches = 0;       // kernels launched by this context
+  bool prof = false;            // bracket GEMM / inverse launches with events
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long k_launches[K_NCLASS] = {0, 0, 0, 0, 0};
+  double k_ms[K_NCLASS] = {0, 0, 0, 0, 0};
+  double k_flops[K_NCLASS] = {0, 0, 0, 0, 0};
+  double k_bytes[K_NCLASS] = {0, 0, 0, 0, 0};
+  cudaEvent_t take_event() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
 };
 
 // error word codes are stored as positive magnitudes with atomicMax

@@ -28,7 +28,9 @@ FP64 = 0
 MIXED = 1
 
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
-           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables"]
+           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_profile_enable",
+           "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse"]
+KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other"]
 
 
 class NegfError(RuntimeError):
@@ -72,6 +74,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                     vp, vp, vp, vp, vp, vp, vp]
     lib.negf_observables.argtypes = [vp, C.POINTER(_System), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_block_gemm.argtypes = [vp, C.c_int, i32, i32, i32, i32, vp, vp, C.c_int64, vp, C.c_int64, vp, vp,
+                                    C.c_int64, vp, C.c_int64, vp]
+    lib.negf_block_inverse.argtypes = [vp, C.c_int, i32, i32, vp, vp, vp, vp]
+    lib.negf_profile_enable.argtypes = [vp, C.c_int]
+    lib.negf_profile_read.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.negf_profile_reset.argtypes = [vp]
     for name in EXPORTS:
         if name != "negf_last_error":
             getattr(lib, name).restype = C.c_int
@@ -120,6 +128,25 @@ class Context:
     def check(self, st):
         if st != NEGF_OK:
             raise NegfError(st, self.lib.negf_last_error(self.h).decode())
+
+    def profile(self, enable: bool):
+        self.check(self.lib.negf_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_reset(self):
+        self.check(self.lib.negf_profile_reset(self.h))
+
+    def profile_read(self) -> dict:
+        """Kernel launches and per-class event timings accumulated since the last reset."""
+        n = len(KERNEL_CLASSES)
+        tot = C.c_int64()
+        kl = (C.c_int64 * n)()
+        ms = (C.c_double * n)()
+        fl = (C.c_double * n)()
+        by = (C.c_double * n)()
+        self.check(self.lib.negf_profile_read(self.h, C.byref(tot), kl, ms, fl, by))
+        return dict(launches=int(tot.value),
+                    classes={k: dict(launches=int(kl[i]), ms=float(ms[i]), flops=float(fl[i]), bytes=float(by[i]))
+                             for i, k in enumerate(KERNEL_CLASSES)})
 
     def sync(self, stream=None) -> int:
         """Synchronize the stream; returns the worst device-side status (0 = OK)."""
@@ -292,3 +319,24 @@ def allocate_outputs(sys: System, lesser=True, device="cuda", want_up_low=True):
                    current=torch.zeros(int(tot[6]), dtype=torch.float64, device=device),
                    density=torch.zeros(int(tot[7]), dtype=torch.float64, device=device))
     return out
+
+
+def negf_block_gemm(ctx: Context, prec, A, B, D, opA=0, opB=0, alpha=1.0, beta=0.0, C_=None, stream=None):
+    """Batched D[u] = alpha op(A[u]) op(B[u]) + beta C[u] on [units, n, n] complex128 tensors
+    (a [n, n] tensor is shared by all units)."""
+    n = D.shape[-1]
+    units = D.shape[0] if D.dim() == 3 else 1
+    st = lambda t: 0 if t.dim() == 2 else n * n
+    al = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (C.c_double * 2)(complex(beta).real, complex(beta).imag)
+    ctx.check(ctx.lib.negf_block_gemm(ctx.h, int(prec), n, units, int(opA), int(opB), al, _ptr(A), st(A), _ptr(B),
+                                      st(B), be, _ptr(C_), st(C_) if C_ is not None else 0, _ptr(D), st(D),
+                                      _stream(stream)))
+
+
+def negf_block_inverse(ctx: Context, prec, M, X, status=None, stream=None):
+    """Batched X[u] = M[u]^{-1} on [units, n, n] complex128 tensors."""
+    n = M.shape[-1]
+    units = M.shape[0] if M.dim() == 3 else 1
+    ctx.check(ctx.lib.negf_block_inverse(ctx.h, int(prec), n, units, _ptr(M), _ptr(X), _ptr(status),
+                                         _stream(stream)))

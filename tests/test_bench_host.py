@@ -1,0 +1,80 @@
+"""Host logic of bench.py on CPU: energy sharding across ranks, the
+max-over-ranks timing reduction (2 gloo ranks), clock parsing, roofline math."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def test_rank_energies_partition_the_grid():
+    ne, world = 1024, 4
+    parts = [bench.rank_energies(ne, r, world) for r in range(world)]
+    assert all(p.size == ne for p in parts)
+    allv = np.sort(np.concatenate(parts))
+    assert np.array_equal(allv, np.linspace(-3.0, 3.0, ne * world))
+    # interleaved: every rank spans the whole window
+    assert all(p.min() < -2.9 and p.max() > 2.9 for p in parts)
+    # one rank is exactly the single-GPU workload
+    assert np.array_equal(bench.rank_energies(ne, 0, 1), np.linspace(-3.0, 3.0, ne))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = bench.max_over_ranks(10.0 + rank, world)
+    e = bench.rank_energies(8, rank, world)
+    bench.barrier(world)
+    q.put((rank, v, e.tolist()))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [11.0, 11.0]
+    e0, e1 = res[0][2], res[1][2]
+    assert not set(e0) & set(e1) and len(e0) == len(e1) == 8
+
+
+def test_clock_summary_parsing():
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1800, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2000, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s["sm_mhz"] == 1900.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_roofline_arithmetic():
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1650.0}
+    st = {"launches": 10, "ms": 20.0, "flops": 10 * 8 * 128 ** 3 * 1024.0, "bytes": 0.0}
+    r = bench.roofline_for("gemm_tc", st, peaks, "measured")
+    per = 8 * 128 ** 3 * 1024.0 / 2e-3 / 1e12
+    assert abs(r["achieved"] - per) < 1e-9
+    assert abs(r["peak"] - 1650.0 * 1.1 / 2.25 / 3) < 1e-9
+    assert abs(r["frac"] - per / r["peak"]) < 1e-12
+    r2 = bench.roofline_for("gemm_f64", st, peaks, "measured")
+    assert r2["bound"] == "alu" and r2["peak"] == 1.25
