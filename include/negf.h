@@ -63,10 +63,15 @@ typedef enum {
 } negf_status;
 
 typedef enum {
-  NEGF_FP64 = 0,   /* every product, inverse and reduction in FP64                        */
-  NEGF_MIXED = 1   /* block GEMMs as 3-term TF32 splits on tcgen05 tensor cores (FP32
-                      accumulate in TMEM); block inverses in FP32 + refinement with an
-                      FP64 residual; inputs/outputs stay complex128                        */
+  NEGF_FP64 = 0,       /* every product, inverse and reduction in FP64                      */
+  NEGF_MIXED = 1,      /* block products on the BF16 tensor cores with exact FP32
+                          accumulation of 7-bit digit slices (FP64-class, ~2^-35 of the
+                          row/column scales); block inverses in FP32 + two refinement steps
+                          whose residual uses the same product; I/O stays complex128        */
+  NEGF_MIXED_TF32 = 2  /* block products as 3-term TF32 splits (hi*hi + hi*lo + lo*hi) on
+                          the tensor cores, FP32 accumulate in TMEM (~1e-6 relative per
+                          128-wide product); inverses FP32 + refinement with an FP64
+                          residual                                                          */
 } negf_precision;
 
 /* One or several independent BT devices. Host struct; device pointers inside. */
@@ -178,16 +183,18 @@ negf_status negf_observables(negf_ctx* ctx, const negf_system* sys,
  * complex128 blocks; X[u] lives at X + u * x_stride (elements; 0 = one block shared
  * by all units).  op: 0 = as stored, 2 = conjugate transpose.  alpha, beta: host
  * double[2] (re, im).  C may be NULL (beta ignored) or equal to D; D must not
- * overlap A or B.  NEGF_FP64: FP64 FMA; NEGF_MIXED: 3-term TF32 split on the
- * tensor cores for n >= 16 (FP64 below). */
+ * overlap A or B.  NEGF_FP64: FP64 FMA; NEGF_MIXED: digit-sliced BF16 tensor-core
+ * product for 16 <= n <= 256; NEGF_MIXED_TF32: 3-term TF32 split for n >= 16
+ * (FP64 FMA outside those ranges). */
 negf_status negf_block_gemm(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, int32_t opA,
                             int32_t opB, const double* alpha, const void* A, int64_t a_stride, const void* B,
                             int64_t b_stride, const double* beta, const void* C, int64_t c_stride, void* D,
                             int64_t d_stride, negf_stream stream);
 /* Batched block inverse X[u] = M[u]^{-1} (unit stride n*n; X may equal M):
  * Gauss-Jordan with partial pivoting (first largest |.| in row order).
- * NEGF_FP64: in FP64.  NEGF_MIXED: in FP32, then one refinement step
- * X <- X + X (I - M X) with the residual formed in FP64.  status (device
+ * NEGF_FP64: in FP64.  NEGF_MIXED / NEGF_MIXED_TF32: in FP32, then two / one
+ * refinement steps X <- X + X (I - M X) with the residual formed with FP64-class
+ * accuracy (the sliced tensor-core product, or FP64 FMA).  status (device
  * int32 [units] or NULL) gets NEGF_ERR_SINGULAR on an exactly zero pivot. */
 negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, const void* M,
                                void* X, int32_t* status, negf_stream stream);
@@ -198,11 +205,12 @@ negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, in
  * accumulates them.  Not a paper operation: measurement support. */
 negf_status negf_profile_enable(negf_ctx* ctx, int enable);
 /* Accumulated since the last reset: `launches` = all kernels this context has
- * launched; per kernel class k (0 = tensor-core GEMM, 1 = FP64 GEMM, 2 = FP32
- * inverse, 3 = FP64 inverse, 4 = other) the launches, total milliseconds,
+ * launched; per kernel class k (0 = TF32-split GEMM, 1 = FP64 GEMM, 2 = FP32
+ * inverse, 3 = FP64 inverse, 4 = other (masked launches), 5 = sliced BF16 GEMM)
+ * the launches, total milliseconds,
  * algorithmic flops (8 n^3 per complex n x n product or inverse, times the
  * units) and algorithmic bytes (16 n^2 per operand read or written).  Each
- * array has 5 entries; any pointer may be NULL. */
+ * array has 6 entries; any pointer may be NULL. */
 negf_status negf_profile_read(negf_ctx* ctx, int64_t* launches, int64_t* k_launches, double* k_ms,
                               double* k_flops, double* k_bytes);
 negf_status negf_profile_reset(negf_ctx* ctx);

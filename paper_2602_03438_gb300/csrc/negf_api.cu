@@ -251,8 +251,9 @@ __global__ void one_minus_kernel(BMat R, int n) {
 struct Engine {
   Ctx* ctx;
   cudaStream_t s;
-  int mixed;
+  int mixed;           // 0: FP64, 1: digit-sliced BF16 tensor-core products, 2: TF32 3-term split
   void* inv_scratch;   // for inverses too large for shared memory
+  void* oz_scratch = nullptr;   // per-row/column scales of the sliced products
   // timing facility: events around one launch of class `cls`
   int open_cls = -1;
   cudaEvent_t open_ev = nullptr;
@@ -280,14 +281,18 @@ struct Engine {
     const double flops = 8.0 * nn * n * units;                        // useful complex flops
     const double bytes = 16.0 * nn * units * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
     cudaError_t e;
-    if (mixed && tc_supported(n)) {
-      begin(K_GEMM_TC);
+    const bool masked = active != nullptr;   // masked launches do an unknown share of the work
+    if (mixed == 1 && oz_supported(n) && oz_scratch) {
+      begin(masked ? K_OTHER : K_GEMM_OZ);
+      e = zgemm_oz(g, oz_scratch, ctx->d_err, s);
+    } else if (mixed == 2 && tc_supported(n)) {
+      begin(masked ? K_OTHER : K_GEMM_TC);
       e = zgemm_tc(g, ctx->d_err, s);
     } else {
-      begin(K_GEMM_F64);
+      begin(masked ? K_OTHER : K_GEMM_F64);
       e = zgemm_f64(g, s);
     }
-    end(flops, bytes);
+    end(masked ? 0.0 : flops, masked ? 0.0 : bytes);
     return e;
   }
   cudaError_t inv(BMat X, BMat M, int n, int units, const int* active, int single, int32_t* status) {
@@ -299,8 +304,11 @@ struct Engine {
   // X = M^{-1}.  Mixed precision: FP32 Gauss-Jordan, then `refine` steps of
   // X <- X + X (I - M X) with the residual I - M X formed in FP64 and the
   // correction product on the engine's GEMM.  T1, T2: scratch slots.
-  cudaError_t inverse(BMat X, BMat M, int n, int units, int32_t* status, BMat T1, BMat T2, int refine = 1) {
-    cudaError_t e = inv(X, M, n, units, nullptr, mixed, status);
+  // Refinement steps: two with the sliced product (each step squares the relative
+  // error of the FP32 inverse, so kappa ~ 1e6 blocks need two), one with the TF32 mode.
+  cudaError_t inverse(BMat X, BMat M, int n, int units, int32_t* status, BMat T1, BMat T2, int refine = -1) {
+    if (refine < 0) refine = (mixed == 1) ? 2 : 1;
+    cudaError_t e = inv(X, M, n, units, nullptr, mixed ? 1 : 0, status);
     if (e != cudaSuccess || !mixed) return e;
     const long long nn = (long long)n * n;
     dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), units);
@@ -309,8 +317,14 @@ struct Engine {
       r.D = T1; r.A = M; r.B = X; r.C = BMat{nullptr, 0};
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
       r.n = n; r.units = units; r.active = nullptr;
-      begin(K_GEMM_F64);
-      e = zgemm_f64(r, s);                                                 // M X   (FP64)
+      // M X with FP64-class accuracy: the sliced tensor-core product, else FP64 FMA
+      if (mixed == 1 && oz_supported(n) && oz_scratch) {
+        begin(K_GEMM_OZ);
+        e = zgemm_oz(r, oz_scratch, ctx->d_err, s);
+      } else {
+        begin(K_GEMM_F64);
+        e = zgemm_f64(r, s);
+      }
       end(8.0 * (double)n * n * n * units, 48.0 * (double)n * n * units);
       if (e != cudaSuccess) return e;
       ++ctx->launches;
@@ -362,7 +376,11 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   zc* gbase = io.GRd ? nullptr : slot(nb);
   zc* glbase = (io.lesser && !io.GLd) ? slot(nb) : nullptr;
   zc* gup_tmp = io.GRu ? nullptr : slot(1);
-  if (eng.inv_scratch == nullptr && zinv_scratch_bytes(b, U, eng.mixed) > 0) eng.inv_scratch = (void*)p;
+  if (zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0) > 0) {
+    eng.inv_scratch = (void*)p;
+    p += zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0);
+  }
+  eng.oz_scratch = (void*)p;
 
   auto S1 = [&](zc* base) { return BMat{base, bb}; };
   // per-energy output blocks: [e][i] with unit stride nb*b*b (diag) or (nb-1)*b*b (off-diagonal)
@@ -450,7 +468,8 @@ size_t rgf_bytes_per_energy(int nb, int b, const RgfIO& io, int mixed) {
   if (io.lesser && !io.GLd) n += nb;
   if (!io.GRu) n += 1;
   size_t bytes = n * blk;
-  bytes += zinv_scratch_bytes(b, 1, mixed);
+  bytes += zinv_scratch_bytes(b, 1, mixed ? 1 : 0);
+  bytes += oz_scratch_bytes(b, 1);
   return bytes;
 }
 
@@ -907,14 +926,15 @@ static negf_status rgf_common(Ctx* ctx, const negf_system* sys, negf_precision p
   negf_status st = make_layout(ctx, sys, L);
   if (st != NEGF_OK) return st;
   if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
-  if (prec != NEGF_FP64 && prec != NEGF_MIXED) return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
   if (!sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "sigma_L and sigma_R are required");
   if (lesser && (!f_L || !f_R)) return fail(ctx, NEGF_ERR_ARG, "f_L and f_R are required for G^<");
   if (scat && scat->per_energy != 0 && scat->per_energy != 1)
     return fail(ctx, NEGF_ERR_ARG, "scattering per_energy must be 0 or 1");
   CU(cudaSetDevice(ctx->device));
   if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * L.off[8 * (size_t)sys->ndev + 2], s));
-  Engine eng{ctx, s, prec == NEGF_MIXED ? 1 : 0, nullptr};
+  Engine eng{ctx, s, (int)prec, nullptr};
   for (int d = 0; d < sys->ndev; ++d) {
     const int ne = sys->ne[d];
     if (ne == 0) continue;
@@ -1252,11 +1272,14 @@ negf_status negf_block_gemm(negf_ctx* c, negf_precision prec, int32_t n, int32_t
   if (n < 1 || n > 4096 || units < 0 || units > 65535) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 4096, 0 <= units <= 65535");
   if ((opA != OP_N && opA != OP_H) || (opB != OP_N && opB != OP_H)) return fail(ctx, NEGF_ERR_ARG, "op must be 0 or 2");
   if (!alpha || !A || !B || !D || (C && !beta)) return fail(ctx, NEGF_ERR_ARG, "NULL operand");
-  if (prec != NEGF_FP64 && prec != NEGF_MIXED) return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
   if (a_stride < 0 || b_stride < 0 || c_stride < 0 || d_stride < 0) return fail(ctx, NEGF_ERR_ARG, "negative stride");
   if (d_stride == 0 && units > 1) return fail(ctx, NEGF_ERR_ARG, "D cannot be shared by several units");
   CU(cudaSetDevice(ctx->device));
-  Engine eng{ctx, (cudaStream_t)stream, prec == NEGF_MIXED ? 1 : 0, nullptr};
+  Engine eng{ctx, (cudaStream_t)stream, (int)prec, nullptr};
+  if (oz_scratch_bytes(n, units) > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small");
+  eng.oz_scratch = ctx->ws;
   CU(eng.gemm(BMat{(zc*)D, d_stride}, BMat{(zc*)A, a_stride}, opA, BMat{(zc*)B, b_stride}, opB,
               zmake(alpha[0], alpha[1]), C ? BMat{(zc*)C, c_stride} : NOMAT,
               C ? zmake(beta[0], beta[1]) : ZERO, n, units));
@@ -1269,19 +1292,22 @@ negf_status negf_block_inverse(negf_ctx* c, negf_precision prec, int32_t n, int3
   if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
   if (n < 1 || n > 512 || units < 0) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 512, units >= 0");
   if (!M || !X) return fail(ctx, NEGF_ERR_ARG, "NULL operand");
-  if (prec != NEGF_FP64 && prec != NEGF_MIXED) return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
   if (units == 0) return NEGF_OK;
   CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int mixed = prec == NEGF_MIXED ? 1 : 0;
+  const int mixed = (int)prec;
   const long long bb = (long long)n * n;
-  // workspace: two scratch slots for the refinement, then the inverse scratch
-  const size_t need = (size_t)units * bb * sizeof(zc) * (mixed ? 2 : 0) + zinv_scratch_bytes(n, units, mixed);
+  // workspace: two scratch slots for the refinement, the inverse scratch, the product scales
+  const size_t inv_b = zinv_scratch_bytes(n, units, mixed ? 1 : 0);
+  const size_t need = (size_t)units * bb * sizeof(zc) * (mixed ? 2 : 0) + inv_b + oz_scratch_bytes(n, units);
   if (need > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for this batch of inverses");
   zc* ws = (zc*)ctx->ws;
   Engine eng{ctx, s, mixed, nullptr};
   BMat T1{ws, bb}, T2{ws + (mixed ? units * bb : 0), bb};
   eng.inv_scratch = (void*)(ws + (mixed ? 2 * units * bb : 0));
+  eng.oz_scratch = (char*)eng.inv_scratch + inv_b;
   if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * units, s));
   CU(eng.inverse(BMat{(zc*)X, bb}, BMat{(zc*)M, bb}, n, units, status, T1, T2));
   return NEGF_OK;

@@ -56,7 +56,7 @@ struct GemmArgs {
 // library context
 // ---------------------------------------------------------------------------
 // kernel classes of the timing facility (negf_profile_*)
-enum KClass { K_GEMM_TC = 0, K_GEMM_F64 = 1, K_INV_F32 = 2, K_INV_F64 = 3, K_OTHER = 4, K_NCLASS = 5 };
+enum KClass { K_GEMM_TC = 0, K_GEMM_F64 = 1, K_INV_F32 = 2, K_INV_F64 = 3, K_OTHER = 4, K_GEMM_OZ = 5, K_NCLASS = 6 };
 
 struct ProfRec {
   int cls;
@@ -76,10 +76,10 @@ struct Ctx {
   bool prof = false;            // bracket GEMM / inverse launches with events
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
-  long long k_launches[K_NCLASS] = {0, 0, 0, 0, 0};
-  double k_ms[K_NCLASS] = {0, 0, 0, 0, 0};
-  double k_flops[K_NCLASS] = {0, 0, 0, 0, 0};
-  double k_bytes[K_NCLASS] = {0, 0, 0, 0, 0};
+  long long k_launches[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double k_ms[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double k_flops[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double k_bytes[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t take_event() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e = nullptr;
@@ -101,6 +101,11 @@ cudaError_t zgemm_f64(const GemmArgs& g, cudaStream_t s);
 // 3-term TF32-split complex GEMM on tcgen05 tensor cores (FP32 accumulate in TMEM)
 cudaError_t zgemm_tc(const GemmArgs& g, int* err, cudaStream_t s);
 bool tc_supported(int n);
+// FP64-class complex GEMM on the BF16 tensor cores (exact-accumulation digit slices);
+// `scratch` holds oz_scratch_bytes(n, units) bytes of per-row/column scales
+cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
+bool oz_supported(int n);
+size_t oz_scratch_bytes(int n, int units);
 
 // X[u] = M[u]^{-1} by Gauss-Jordan with partial pivoting (first max |.| in row
 // order).  FP64, or FP32 (`single` != 0) with the result written back in FP64.

@@ -26,11 +26,12 @@ NEGF_ERR_SINGULAR = -5
 NEGF_ERR_TIMEOUT = -6
 FP64 = 0
 MIXED = 1
+MIXED_TF32 = 2
 
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
            "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_profile_enable",
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse"]
-KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other"]
+KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
 
 
 class NegfError(RuntimeError):

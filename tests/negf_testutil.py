@@ -11,6 +11,21 @@ TOL_FP64 = 1e-10
 TOL_MIXED = 1e-6
 
 
+GR_KEYS = ("GR_diag", "GR_up", "GR_low")
+GL_KEYS = ("GL_diag", "GL_low")
+
+
+def gf_err(r, e, ref, keys):
+    """Normwise error of one Green's function over its whole BT pattern for energy e:
+    max over all its blocks of ||got - ref||_F / max over all its blocks of ||ref||_F."""
+    num, den = 0.0, 0.0
+    for k in keys:
+        for i in range(ref[k].shape[0]):
+            num = max(num, np.linalg.norm(r[k][e][i] - ref[k][i]))
+            den = max(den, np.linalg.norm(ref[k][i]))
+    return num / max(den, 1e-300)
+
+
 def block_err(got, ref):
     """max_i ||got_i - ref_i||_F / max_i ||ref_i||_F over the blocks of one energy."""
     if ref.size == 0:

@@ -8,7 +8,8 @@ import torch
 
 import workloads as W
 from oracle import negf_oracle as O
-from negf_testutil import TOL_FP64, TOL_MIXED, block_err, oracle_density, run_gpu, strong_leads
+from negf_testutil import (GL_KEYS, GR_KEYS, TOL_FP64, TOL_MIXED, block_err, gf_err, oracle_density, run_gpu,
+                           strong_leads)
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +31,23 @@ def ctx(P):
 
 
 def _check_energy(r, e, ref, tol, lesser=True, keys=None):
+    """FP64: every output family on its own (max block error / max block norm)."""
     keys = keys or (["GR_diag", "GR_up", "GR_low"] + (["GL_diag", "GL_low"] if lesser else []))
     for k in keys:
         err = block_err(r[k][e], ref[k])
         assert err <= tol, (k, e, err)
+
+
+def _check_energy_mixed(r, e, ref, tol, lesser=True, keys=None):
+    """Mixed precision: normwise over the BT pattern of G^R and of G^< (the products
+    are accurate relative to row/column scales, not to blocks that are 1e-30 of
+    their neighbours)."""
+    gr = [k for k in GR_KEYS if keys is None or k in keys]
+    gl = [k for k in GL_KEYS if keys is None or k in keys] if lesser else []
+    for ks in (gr, gl):
+        if ks:
+            err = gf_err(r, e, ref, ks)
+            assert err <= tol, (ks, e, err)
 
 
 # --- config 1, in full -----------------------------------------------------------
@@ -65,7 +79,7 @@ def test_config1_mixed_full(P, ctx):
     assert np.all(r["status"] == 0)
     for e in range(dev.ne):
         ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
-        _check_energy(r, e, ref, TOL_MIXED)
+        _check_energy_mixed(r, e, ref, TOL_MIXED)
 
 
 # --- shape sweep: tiles, ragged tails, degenerate sizes --------------------------
@@ -101,7 +115,17 @@ def test_shapes_mixed_lesser(P, ctx, nb, b):
     r = run_gpu(P, ctx, dev, P.MIXED)[0]
     for e in range(dev.ne):
         ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
-        _check_energy(r, e, ref, TOL_MIXED)
+        _check_energy_mixed(r, e, ref, TOL_MIXED)
+
+
+@pytest.mark.parametrize("nb", [4, 9])
+def test_banded_weak_coupling_mixed(P, ctx, nb):
+    """The config-2 generator itself (corner-coupled blocks, G^< spanning 30 decades)."""
+    dev = W.banded_device(nb, 128, 8, seed=77, overlap=True)
+    r = run_gpu(P, ctx, dev, P.MIXED)[0]
+    for e in range(dev.ne):
+        ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
+        _check_energy_mixed(r, e, ref, TOL_MIXED)
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
@@ -113,7 +137,7 @@ def test_scattering_lesser(P, ctx, prec):
     r = run_gpu(P, ctx, dev, p)[0]
     for e in range(dev.ne):
         ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
-        _check_energy(r, e, ref, tol)
+        (_check_energy if prec == "FP64" else _check_energy_mixed)(r, e, ref, tol)
         # J is a small difference of large terms: scale by the size of its summands
         jscale = max(np.linalg.norm(dev.H_up[i]) * np.linalg.norm(ref["GL_low"][i]) for i in range(dev.nb - 1))
         assert np.abs(r["current"][e] - ref["J"]).max() <= tol * jscale
@@ -131,7 +155,8 @@ def test_nb1_with_given_sigma(P, ctx):
         r = run_gpu(P, ctx, dev, prec, obc=False, sigma=(sig[0], sig[1]), obs=False)[0]
         for e in range(dev.ne):
             ref = O.solve_energy(dev, e, sigma=(sig[0][e], sig[1][e]))
-            _check_energy(r, e, ref, tol, keys=["GR_diag", "GL_diag"])
+            chk = _check_energy if prec == P.FP64 else _check_energy_mixed
+            chk(r, e, ref, tol, keys=["GR_diag", "GL_diag"])
 
 
 def test_uneven_batch_matches_single_devices(P, ctx):
