@@ -199,6 +199,36 @@ negf_status negf_block_gemm(negf_ctx* ctx, negf_precision prec, int32_t n, int32
 negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, const void* M,
                                void* X, int32_t* status, negf_stream stream);
 
+/* No-allocation variant of negf_block_gemm with NEGF_MIXED precision.
+ *
+ * No counterpart in the paper: this is a service for callers that cannot allocate
+ * device memory -- an application that owns all device memory through its own
+ * arena and forbids libraries to allocate, or a latency-critical loop that cannot
+ * afford the device synchronization of cudaMalloc / cudaFree.  Such callers cannot
+ * create a negf_ctx (whose workspace is allocated), so this call takes no context
+ * and allocates nothing.  The caller passes every input and output, with the same
+ * meaning and layout as negf_block_gemm; `stream` is any stream of the current
+ * device.
+ *
+ * The only scratch, the per-row / per-column scale exponents of the sliced product
+ * (4 bytes x 2 n per unit, for 16 <= n <= 227), lives in a static device array of
+ * NEGF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Calls with 2 n units x 4 bytes above that size are rejected with
+ * NEGF_ERR_ARG and a message from negf_last_error(NULL); split the batch.  Other n
+ * use FP64 FMA and no scratch.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (every scale a call reads is written by that same
+ * call first, so nothing needs clearing); calls whose kernels overlap on the GPU
+ * (other streams) race on it -- serialize them.  `status` (device int32 or NULL)
+ * receives, through atomicMax, the magnitude of NEGF_ERR_TIMEOUT if a device-side
+ * wait ran out; the caller clears it. */
+#define NEGF_NOALLOC_SCRATCH_BYTES (1u << 20)
+negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t opA, int32_t opB, const double* alpha,
+                                    const void* A, int64_t a_stride, const void* B, int64_t b_stride,
+                                    const double* beta, const void* C, int64_t c_stride, void* D,
+                                    int64_t d_stride, int32_t* status, negf_stream stream);
+
 /* Kernel timing (the tracing facility).  When enabled, every launch of the
  * block-GEMM and block-inverse kernels is bracketed by CUDA events recorded on
  * the launch stream; negf_profile_read() synchronizes on those events and

@@ -842,6 +842,8 @@ __global__ void density_accum_kernel(const double* nE, const double* w, int e0, 
 
 }  // namespace
 
+void negf::negf_set_error_message(const char* msg) { g_tls_error = msg ? msg : ""; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -116,4 +116,7 @@ cudaError_t zinv(BMat X, BMat M, int n, int units, const int* active, int single
                  int32_t* status, cudaStream_t s);
 size_t zinv_scratch_bytes(int n, int units, int single);
 
+// sets the thread-local message returned by negf_last_error(NULL)
+void negf_set_error_message(const char* msg);
+
 }  // namespace negf

@@ -30,7 +30,8 @@ MIXED_TF32 = 2
 
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
            "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_profile_enable",
-           "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse"]
+           "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
+           "negf_block_gemm_noalloc"]
 KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
 
 
@@ -78,6 +79,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_block_gemm.argtypes = [vp, C.c_int, i32, i32, i32, i32, vp, vp, C.c_int64, vp, C.c_int64, vp, vp,
                                     C.c_int64, vp, C.c_int64, vp]
     lib.negf_block_inverse.argtypes = [vp, C.c_int, i32, i32, vp, vp, vp, vp]
+    lib.negf_block_gemm_noalloc.argtypes = [i32, i32, i32, i32, vp, vp, C.c_int64, vp, C.c_int64, vp, vp,
+                                            C.c_int64, vp, C.c_int64, vp, vp]
     lib.negf_profile_enable.argtypes = [vp, C.c_int]
     lib.negf_profile_read.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.negf_profile_reset.argtypes = [vp]
@@ -341,3 +344,19 @@ def negf_block_inverse(ctx: Context, prec, M, X, status=None, stream=None):
     units = M.shape[0] if M.dim() == 3 else 1
     ctx.check(ctx.lib.negf_block_inverse(ctx.h, int(prec), n, units, _ptr(M), _ptr(X), _ptr(status),
                                          _stream(stream)))
+
+
+def negf_block_gemm_noalloc(A, B, D, opA=0, opB=0, alpha=1.0, beta=0.0, C_=None, status=None, stream=None):
+    """The NEGF_MIXED block product without a context or any allocation (static
+    device scratch); same operands as negf_block_gemm."""
+    lib = load_library()
+    n = D.shape[-1]
+    units = D.shape[0] if D.dim() == 3 else 1
+    st = lambda t: 0 if t.dim() == 2 else n * n
+    al = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (C.c_double * 2)(complex(beta).real, complex(beta).imag)
+    rc = lib.negf_block_gemm_noalloc(n, units, int(opA), int(opB), al, _ptr(A), st(A), _ptr(B), st(B), be,
+                                     _ptr(C_), st(C_) if C_ is not None else 0, _ptr(D), st(D), _ptr(status),
+                                     _stream(stream))
+    if rc != NEGF_OK:
+        raise NegfError(rc, lib.negf_last_error(None).decode())
