@@ -78,3 +78,12 @@ def test_roofline_arithmetic():
     assert abs(r["frac"] - per / r["peak"]) < 1e-12
     r2 = bench.roofline_for("gemm_f64", st, peaks, "measured")
     assert r2["bound"] == "alu" and r2["peak"] == 1.25
+
+
+def test_roofline_sliced_gemm_counts_tensor_work():
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1650.0}
+    st = {"launches": 4, "ms": 8.0, "flops": 4 * 8 * 128 ** 3 * 100.0, "bytes": 0.0}
+    r = bench.roofline_for("gemm_oz", st, peaks, "measured")
+    useful = 8 * 128 ** 3 * 100.0 / 2e-3 / 1e12
+    assert abs(r["useful_tflops"] - useful) < 1e-9
+    assert abs(r["achieved"] - 28 * useful) < 1e-9 and r["peak"] == 1650.0
