@@ -65,8 +65,8 @@ typedef enum {
 typedef enum {
   NEGF_FP64 = 0,       /* every product, inverse and reduction in FP64                      */
   NEGF_MIXED = 1,      /* block products on the BF16 tensor cores with exact FP32
-                          accumulation of 7-bit digit slices (FP64-class, ~2^-35 of the
-                          row/column scales); block inverses in FP32 + two refinement steps
+                          accumulation of 7-bit digit slices (FP64-class, ~2^-55 of the
+                          row/column scales, 16 <= b <= 256; FP64 FMA otherwise); block inverses in FP32 + two refinement steps
                           whose residual uses the same product; I/O stays complex128        */
   NEGF_MIXED_TF32 = 2  /* block products as 3-term TF32 splits (hi*hi + hi*lo + lo*hi) on
                           the tensor cores, FP32 accumulate in TMEM (~1e-6 relative per
@@ -211,7 +211,7 @@ negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, in
  * device.
  *
  * The only scratch, the per-row / per-column scale exponents of the sliced product
- * (4 bytes x 2 n per unit, for 16 <= n <= 227), lives in a static device array of
+ * (4 bytes x 2 n per unit, for 16 <= n <= 256), lives in a static device array of
  * NEGF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  Calls with 2 n units x 4 bytes above that size are rejected with
  * NEGF_ERR_ARG and a message from negf_last_error(NULL); split the batch.  Other n

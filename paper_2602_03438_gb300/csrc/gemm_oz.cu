@@ -10,23 +10,23 @@
 //
 // Scheme (error-free slicing in the manner of Ozaki et al.):
 //  * every row m of op(A') and column j of op(B') gets a power-of-two scale 2^e
-//    with all its entries below it (A' = [Re A | Im A], B' = [[Re B, Im B],
+//    with all its entries below 2^(e-1) (A' = [Re A | Im A], B' = [[Re B, Im B],
 //    [-Im B, Re B]] as in the TF32 kernel);
-//  * each real entry x becomes X = rint(x 2^(49-e)) and is cut into balanced
-//    base-2^7 digits d1 (|d1| <= 128) and d2..d7 (|d| <= 64): X = sum d_s 2^(7(7-s)),
-//    all exact in BF16;
-//  * the slice products A_s B_t with s + t = d <= 8 (28 pairs) are summed into one
-//    FP32 accumulator per d (7 accumulators in TMEM).  With K = 2n real terms the
-//    largest group sum is (2*128*64 + 5*64*64) * 2n < 2^24 for n <= 227: exact;
-//  * the epilogue forms sum_d G_d 2^(7(8-d)) as two exact int64 halves, rebuilds
-//    each double with integer operations, scaled by 2^(e_A + e_B - 56), and adds them.
-// The error is ~2^-49 of |row of A| |column of B| (truncation of the digits and of
-// the pairs with s + t > 8): FP64-class for the RGF tolerances.  (Rows and columns
+//  * each real entry x becomes X = rint(x 2^(56-e)) (|X| <= 2^55) and is cut into
+//    balanced base-2^7 digits d1..d8 with |d| <= 64: X = sum d_s 2^(7(8-s)), all
+//    exact in BF16;
+//  * the slice products A_s B_t with s + t = d <= 9 (36 pairs) are summed into one
+//    FP32 accumulator per d (8 accumulators in TMEM).  With K = 2n real terms the
+//    largest group sum is 8 * 64 * 64 * 2n < 2^24 for n <= 256: exact;
+//  * the epilogue forms sum_d G_d 2^(7(9-d)) as two exact int64 halves, rebuilds
+//    each double with integer operations, scaled by 2^(e_A + e_B - 63), and adds them.
+// The error is ~2^-55 of |row of A| |column of B| (truncation of the digits and of
+// the pairs with s + t > 9): FP64-class for the RGF tolerances.  (Rows and columns
 // keep their own scales; entries far below their row's or column's largest entry
 // keep an absolute, not a relative, accuracy.)
 //
 // Tile: 128 rows x 32 complex columns (N = 64 real: 32 real parts, 32 imaginary
-// parts; 7 accumulators x 64 columns fit the 512 TMEM columns), K chunks of 16
+// parts; 8 accumulators x 64 columns fill the 512 TMEM columns), K chunks of 16
 // complex (32 real = 64-byte rows, 64B swizzle), two shared-memory stages.
 #include "negf_internal.cuh"
 
@@ -38,15 +38,15 @@ constexpr int TM = 128;                 // rows per tile
 constexpr int TNC = 32;                 // complex columns per tile
 constexpr int NR = 2 * TNC;             // real MMA columns (64)
 constexpr int KC = 16;                  // complex K per chunk
-constexpr int NS = 7;                   // digits per value
-constexpr int NG = 7;                   // scale groups d = 2..8
+constexpr int NS = 8;                   // digits per value
+constexpr int NG = 8;                   // scale groups d = 2..9
 constexpr int NPAIR = NS * (NS + 1) / 2;   // slice pairs with s + t <= NS + 1
-constexpr int HSPLIT = 3;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
+constexpr int HSPLIT = 4;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
 constexpr int NT = 256;
 constexpr uint32_t ROWB = 64;                            // bytes per smem row (32 bf16)
 constexpr uint32_t A_SLICE = TM * ROWB;                  // 8 KB
 constexpr uint32_t B_SLICE = NR * ROWB;                  // 4 KB
-constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);     // 84 KB
+constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);     // 96 KB
 constexpr uint32_t SMEM_BYTES = 2 * STAGE + 1024 + 64;
 constexpr unsigned long long kSpinLimit = 1ull << 28;
 
@@ -107,41 +107,54 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  "=r"(r[7])                                                                       \
                : "r"(taddr))
 
-// scale exponent: smallest e with |v| < 2^e for the largest component magnitude v (0 if v == 0)
+// scale exponent: e with |v| < 2^(e-1) for the largest component magnitude v, so that
+// the top digit stays within 64 (0 if v == 0)
 __device__ __forceinline__ int scale_exp(double v) {
   if (!(v > 0.0)) return 0;
   int e;
   frexp(v, &e);
-  return e;
+  return e + 1;
 }
 
-// digits of x at scale 2^e (|x| < 2^e): X = rint(x 2^(7 NS - e)) = sum d_s 2^(7(NS-1-s))
+// digits of x at scale 2^e (|x| < 2^(e-1)): X = rint(|x| 2^(7 NS - e)) <= 2^55 is cut
+// into base-2^7 fields from the least significant one up, each carried into a
+// balanced digit (|d| <= 64); d[0] is the most significant, and the sign of x is
+// applied to every digit
 __device__ __forceinline__ void digits(double x, int e, int d[NS]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
-  long long X = 0;
+  unsigned long long X = 0;
   if (ex != 0) {
     const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    // X = mant * 2^(ex - 1075 + 7 NS - e); |x| < 2^e makes the right shift >= 4
-    const int rs = 1075 - 7 * NS + e - ex;
-    if (rs < 63) {
-      const unsigned long long r = rs > 0 ? ((mant + (1ull << (rs - 1))) >> rs) : mant;
-      X = (bits >> 63) ? -(long long)r : (long long)r;
-    }
+    const int rs = 1075 - 7 * NS + e - ex;   // >= -2 because |x| < 2^(e-1)
+    if (rs <= 0) X = mant << (-rs);
+    else if (rs < 64) X = (mant + (1ull << (rs - 1))) >> rs;
   }
+  const unsigned int lo = (unsigned int)X, hi = (unsigned int)(X >> 32);
+  int carry = 0;
 #pragma unroll
   for (int k = 0; k < NS - 1; ++k) {
-    const int sh = 7 * (NS - 1 - k);
-    const long long q = (X + (1ll << (sh - 1))) >> sh;   // balanced digit
-    d[k] = (int)q;
-    X -= q << sh;
+    const int sh = 7 * k;
+    unsigned int f;
+    if (sh + 7 <= 32) f = (lo >> sh) & 127u;
+    else if (sh >= 32) f = (hi >> (sh - 32)) & 127u;
+    else f = __funnelshift_r(lo, hi, sh) & 127u;
+    const int v = (int)f + carry;
+    carry = v >= 64 ? 1 : 0;
+    d[NS - 1 - k] = v - (carry << 7);
   }
-  d[NS - 1] = (int)X;
+  d[0] = (int)(X >> (7 * (NS - 1))) + carry;
+  if (bits >> 63) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) d[k] = -d[k];
+  }
 }
 
-__device__ __forceinline__ unsigned short bf16_of_int(int v) {
-  // small integers (|v| <= 256) are exact in BF16: the top half of their FP32 pattern
-  return (unsigned short)(__float_as_uint((float)v) >> 16);
+// BF16 bit pattern of a small integer (|v| <= 256, exact): 1.5*2^23 + v keeps the float
+// in [2^23, 2^24) where its spacing is 1, so adding v to the bit pattern and
+// subtracting 1.5*2^23 gives (float)v exactly; the top 16 bits are the BF16 value
+__device__ __forceinline__ unsigned int bf16_of_int(int v) {
+  return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f) >> 16;
 }
 
 // exact int64 (|v| < 2^53) times 2^p as an IEEE double, built with integer operations
@@ -194,24 +207,6 @@ __global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb) {
   }
 }
 
-// pairs (s, t) of 0-based digits with s + t <= NS - 1, ordered by group s + t; the
-// first pair of each group initializes its accumulator
-struct PairTable {
-  int s[NPAIR], t[NPAIR], first[NPAIR];
-};
-__host__ __device__ constexpr PairTable make_pairs() {
-  PairTable p{};
-  int k = 0;
-  for (int g = 0; g < NS; ++g)
-    for (int s = 0; s <= g; ++s) {
-      p.s[k] = s;
-      p.t[k] = g - s;
-      p.first[k] = (s == 0) ? 1 : 0;
-      ++k;
-    }
-  return p;
-}
-__constant__ PairTable kPairs = make_pairs();
 
 __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* ea, const int* eb, int* err,
                                                         int unit_alpha_beta) {
@@ -250,6 +245,33 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
   const uint32_t tmem = *tmem_slot;
 
   const int nchunks = (n + KC - 1) / KC;
+  // work items: A -- row am, 8 consecutive complex k from ak (every thread);
+  // B -- column bn, 4 consecutive complex k from bk (threads 0 .. 4*TNC-1)
+  const int am = tid >> 1, ak = (tid & 1) * 8;
+  const bool has_b = tid < 4 * TNC;
+  const int bn = (tid >> 2) & (TNC - 1), bk = (tid & 3) * 4;
+  const int gm = m0 + am, gn = n0 + bn;
+  const int ea_m = (gm < n) ? eA[gm] : 0;
+  const int eb_n = (has_b && gn < n) ? eB[gn] : 0;
+  zc ra[8], rb[4];
+  auto load = [&](int c) {
+    const int k0 = c * KC;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gk = k0 + ak + j;
+      ra[j] = zmake(0.0, 0.0);
+      if (gm < n && gk < n) ra[j] = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+    }
+    if (has_b) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + bk + j;
+        rb[j] = zmake(0.0, 0.0);
+        if (gn < n && gk < n) rb[j] = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+      }
+    }
+  };
+  if (nchunks > 0) load(0);
   bool ok = true;
   for (int c = 0; c < nchunks; ++c) {
     const int s = c & 1;
@@ -261,67 +283,88 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
     unsigned char* st = base + s * STAGE;
     unsigned char* Asl = st;                       // NS planes of A_SLICE
     unsigned char* Bsl = st + NS * A_SLICE;        // NS planes of B_SLICE
-    const int k0 = c * KC;
-    // ---- A' digits: rows m0..m0+127, complex k0..k0+15 (real part -> col kk, imaginary -> 16+kk)
-    for (int it = 0; it < (TM * KC) / NT; ++it) {
-      int mm, kk;
-      if (g.opA == OP_N) { kk = tid & 15; mm = (tid >> 4) + 16 * it; }
-      else { mm = tid & 127; kk = (tid >> 7) + 2 * it; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      zc v = zmake(0.0, 0.0);
-      int e = 0;
-      if (gm < n && gk < n) {
-        v = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
-        e = eA[gm];
+    // this chunk's entries; the next chunk's loads are issued before digitizing
+    zc ca[8], cb[4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ca[j] = ra[j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cb[j] = rb[j];
+    if (c + 1 < nchunks) load(c + 1);
+    // ---- A': real part -> columns ak..ak+7, imaginary part -> 16+ak..; 16-byte stores
+    {
+      unsigned int pr[NS][4], pi[NS][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int dr[NS], di[NS];
+        digits(ca[j].x, ea_m, dr);
+        digits(ca[j].y, ea_m, di);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (j & 1) {
+            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
+            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+          } else {
+            pr[q][j >> 1] = bf16_of_int(dr[q]);
+            pi[q][j >> 1] = bf16_of_int(di[q]);
+          }
+        }
       }
-      int dr[NS], di[NS];
-      digits(v.x, e, dr);
-      digits(v.y, e, di);
-      const uint32_t o_r = sw64(mm, kk), o_i = sw64(mm, KC + kk);
+      const uint32_t o_r = sw64(am, ak), o_i = sw64(am, KC + ak);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
-        *reinterpret_cast<unsigned short*>(Asl + q * A_SLICE + o_r) = bf16_of_int(dr[q]);
-        *reinterpret_cast<unsigned short*>(Asl + q * A_SLICE + o_i) = bf16_of_int(di[q]);
+        *reinterpret_cast<uint4*>(Asl + q * A_SLICE + o_r) = make_uint4(pr[q][0], pr[q][1], pr[q][2], pr[q][3]);
+        *reinterpret_cast<uint4*>(Asl + q * A_SLICE + o_i) = make_uint4(pi[q][0], pi[q][1], pi[q][2], pi[q][3]);
       }
     }
-    // ---- B'^T digits: row nn: [Re | -Im] of column n0+nn;  row 48+nn: [Im | Re]
-    for (int idx = tid; idx < TNC * KC; idx += NT) {
-      int nn, kk;
-      if (g.opB == OP_N) { nn = idx % TNC; kk = idx / TNC; }
-      else { kk = idx & 15; nn = idx >> 4; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      zc v = zmake(0.0, 0.0);
-      int e = 0;
-      if (gn < n && gk < n) {
-        v = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
-        e = eB[gn];
+    // ---- B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC+bn: [Im | Re]; 8-byte stores
+    if (has_b) {
+      unsigned int pr[NS][2], pi[NS][2];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int dr[NS], di[NS];
+        digits(cb[j].x, eb_n, dr);
+        digits(cb[j].y, eb_n, di);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (j & 1) {
+            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
+            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+          } else {
+            pr[q][j >> 1] = bf16_of_int(dr[q]);
+            pi[q][j >> 1] = bf16_of_int(di[q]);
+          }
+        }
       }
-      int dr[NS], di[NS];
-      digits(v.x, e, dr);
-      digits(v.y, e, di);
-      const uint32_t o1 = sw64(nn, kk), o2 = sw64(nn, KC + kk), o3 = sw64(TNC + nn, kk), o4 = sw64(TNC + nn, KC + kk);
+      const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         unsigned char* P = Bsl + q * B_SLICE;
-        *reinterpret_cast<unsigned short*>(P + o1) = bf16_of_int(dr[q]);
-        *reinterpret_cast<unsigned short*>(P + o2) = bf16_of_int(-di[q]);
-        *reinterpret_cast<unsigned short*>(P + o3) = bf16_of_int(di[q]);
-        *reinterpret_cast<unsigned short*>(P + o4) = bf16_of_int(dr[q]);
+        *reinterpret_cast<uint2*>(P + o1) = make_uint2(pr[q][0], pr[q][1]);
+        *reinterpret_cast<uint2*>(P + o2) = make_uint2(pi[q][0] ^ 0x80008000u, pi[q][1] ^ 0x80008000u);
+        *reinterpret_cast<uint2*>(P + o3) = make_uint2(pi[q][0], pi[q][1]);
+        *reinterpret_cast<uint2*>(P + o4) = make_uint2(pr[q][0], pr[q][1]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aB = smem_u32(Asl), bB = smem_u32(Bsl);
-#pragma unroll 1
-      for (int p = 0; p < NPAIR; ++p) {
-        const int ps = kPairs.s[p], pt = kPairs.t[p];
-        const uint32_t dcol = (uint32_t)((ps + pt) * NR);
+      // descriptors of slice 0 at k-step 0; the others differ by compile-time address
+      // offsets, added to the start-address field (16-byte units, no carry out of it)
+      const uint64_t da = sdesc64(smem_u32(Asl)), db = sdesc64(smem_u32(Bsl));
+      const uint32_t first_chunk = (c == 0) ? 1u : 0u;
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {   // K = 16 bf16 (32 bytes) per instruction
-          const uint32_t acc = (c > 0 || ks > 0 || !kPairs.first[p]) ? 1u : 0u;
-          mma_bf16(tmem + dcol, sdesc64(aB + ps * A_SLICE + ks * 32), sdesc64(bB + pt * B_SLICE + ks * 32), acc);
+      for (int gsum = 0; gsum < NS; ++gsum) {        // scale group s + t
+#pragma unroll
+        for (int ps = 0; ps <= gsum; ++ps) {
+          const int pt = gsum - ps;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {           // K = 16 bf16 (32 bytes) per instruction
+            const uint32_t acc = (ps == 0 && ks == 0) ? (first_chunk ^ 1u) : 1u;
+            mma_bf16(tmem + (uint32_t)(gsum * NR),
+                     da + (uint64_t)((ps * A_SLICE + ks * 32) >> 4),
+                     db + (uint64_t)((pt * B_SLICE + ks * 32) >> 4), acc);
+          }
         }
       }
       mma_commit(&bars[s]);
@@ -409,8 +452,8 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
 
 }  // namespace
 
-// exact group sums need (2*128*64 + (NS-2)*64*64) * 2n < 2^24
-bool oz_supported(int n) { return n >= 16 && n <= 227; }
+// exact group sums need NS * 64 * 64 * 2n < 2^24
+bool oz_supported(int n) { return n >= 16 && n <= 256; }
 
 size_t oz_scratch_bytes(int n, int units) { return sizeof(int) * 2 * (size_t)n * units; }
 

@@ -118,6 +118,20 @@ def test_shapes_mixed_lesser(P, ctx, nb, b):
         _check_energy_mixed(r, e, ref, TOL_MIXED)
 
 
+def test_uneven_batch_mixed_block_sizes(P, ctx):
+    """Config-3 style: devices with different block sizes (incl. 192, 256) and block
+    counts in one call, mixed precision, each against the oracle."""
+    shapes = [(3, 32, 4), (2, 96, 3), (2, 192, 2), (2, 256, 2), (5, 64, 0)]
+    devs = [strong_leads(W.banded_device(nb, b, ne, seed=300 + k, overlap=True), seed=k)
+            for k, (nb, b, ne) in enumerate(shapes)]
+    rs = run_gpu(P, ctx, devs, P.MIXED)
+    for dev, r in zip(devs, rs):
+        assert np.all(r["obc_status"] == 0)
+        for e in range(dev.ne):
+            ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
+            _check_energy_mixed(r, e, ref, TOL_MIXED)
+
+
 @pytest.mark.parametrize("nb", [4, 9])
 def test_banded_weak_coupling_mixed(P, ctx, nb):
     """The config-2 generator itself (corner-coupled blocks, G^< spanning 30 decades)."""
