@@ -28,6 +28,8 @@
 // Tile: 128 rows x 32 complex columns (N = 64 real: 32 real parts, 32 imaginary
 // parts; 8 accumulators x 64 columns fill the 512 TMEM columns), K chunks of 16
 // complex (32 real = 64-byte rows, 64B swizzle), two shared-memory stages.
+#include <stdlib.h>
+
 #include "negf_internal.cuh"
 
 namespace negf {
@@ -43,12 +45,13 @@ constexpr int NG = 8;                   // scale groups d = 2..9
 constexpr int NPAIR = NS * (NS + 1) / 2;   // slice pairs with s + t <= NS + 1
 constexpr int HSPLIT = 4;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
 constexpr int NT = 256;
+constexpr int kCluster = 4;            // column tiles sharing one A tile's digits
 constexpr uint32_t ROWB = 64;                            // bytes per smem row (32 bf16)
 constexpr uint32_t A_SLICE = TM * ROWB;                  // 8 KB
 constexpr uint32_t B_SLICE = NR * ROWB;                  // 4 KB
 constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);     // 96 KB
 constexpr uint32_t SMEM_BYTES = 2 * STAGE + 1024 + 64;
-constexpr unsigned long long kSpinLimit = 1ull << 28;
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -84,16 +87,75 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// acquire at cluster scope: the phase was completed by arrivals from other members
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kWaitNs) return false;
+  }
+}
+// arrive (release, cluster scope) on an mbarrier of another member (shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// bounded wait: gives up after kWaitNs of GPU time (the caller records the timeout)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned long long i = 0; i < kSpinLimit; ++i)
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared::cta offset in member `rank`
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+// all threads of all member CTAs
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+// completion of this thread's MMAs arrives on the same barrier offset in every member of ctaMask
+__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -173,11 +235,11 @@ __device__ __forceinline__ double ldexp_int(long long v, int p) {
 // ---------------------------------------------------------------------------
 // scale pre-pass: ea[u][m] for rows of op(A), eb[u][j] for columns of op(B)
 // ---------------------------------------------------------------------------
-__global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb) {
+__global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb, int first) {
   const int u = blockIdx.y;
   if (g.active && !g.active[u]) return;
   const int n = g.n;
-  const bool forA = blockIdx.x == 0;
+  const bool forA = blockIdx.x + first == 0;
   const zc* M = forA ? g.A.at(u) : g.B.at(u);
   const int op = forA ? g.opA : g.opB;
   int* out = (forA ? ea : eb) + (size_t)u * n;
@@ -208,16 +270,27 @@ __global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb) {
 }
 
 
-__global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* ea, const int* eb, int* err,
-                                                        int unit_alpha_beta) {
+// CL CTAs of a cluster are the CL column tiles of one 128-row tile (grid x is padded to a
+// multiple of CL): each digitizes TM/CL of the A rows into every member's shared memory
+//
+// Warp roles: warps 0..7 produce digits (and run the epilogue), warp 8 issues the MMAs.
+// Handshakes are mbarriers only: full[s] collects one arrival per producer warp of every
+// member (their stores into this member's stage s are done), empty[s] one multicast
+// commit per member (its MMAs reading stage s are done; they read A rows that this
+// member wrote).
+template <int CL>
+__global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const int* ea, const int* eb, int* err,
+                                                             int unit_alpha_beta) {
   const int u = blockIdx.z;
   if (g.active && !g.active[u]) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE + 32);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE);   // full[2], empty[2], done
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE + 48);
   __shared__ int s_fail;
-  __shared__ int s_wait_ok;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = g.n;
@@ -228,8 +301,11 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
   const int* eB = eb + (size_t)u * n;
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    mbar_init(&full[0], 8 * CL);
+    mbar_init(&full[1], 8 * CL);
+    mbar_init(&empty[0], CL);
+    mbar_init(&empty[1], CL);
+    mbar_init(done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -244,97 +320,122 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
+  const uint32_t rank = cluster_ctarank();
+  const uint32_t lbase = smem_u32(base);
+  uint32_t rbase[CL];
+#pragma unroll
+  for (int r = 0; r < CL; ++r) rbase[r] = mapa_shared(lbase, (uint32_t)r);
+  cluster_sync();   // every member is resident (barriers initialized) before remote stores
+
   const int nchunks = (n + KC - 1) / KC;
-  // work items: A -- row am, 8 consecutive complex k from ak (every thread);
-  // B -- column bn, 4 consecutive complex k from bk (threads 0 .. 4*TNC-1)
-  const int am = tid >> 1, ak = (tid & 1) * 8;
-  const bool has_b = tid < 4 * TNC;
-  const int bn = (tid >> 2) & (TNC - 1), bk = (tid & 3) * 4;
+  // work items: threads 0..127 -- A row am (this member's share), AK consecutive
+  // complex k from ak; threads 128..255 -- B column bn, 4 consecutive complex k from bk
+  constexpr int AK = 16 / (128 / (TM / CL));   // 4 for CL = 4, 8 for CL = 2
+  const bool is_a = tid < 128;
+  const int it = tid & 127;
+  const int am = (int)rank * (TM / CL) + it / (KC / AK), ak = (it % (KC / AK)) * AK;
+  const int bn = it >> 2, bk = (it & 3) * 4;
   const int gm = m0 + am, gn = n0 + bn;
-  const int ea_m = (gm < n) ? eA[gm] : 0;
-  const int eb_n = (has_b && gn < n) ? eB[gn] : 0;
-  zc ra[8], rb[4];
+  const int escale = is_a ? ((gm < n) ? eA[gm] : 0) : ((gn < n) ? eB[gn] : 0);
+  constexpr int NV = (AK > 4) ? AK : 4;   // complex entries held per thread
+  zc rv[NV];
   auto load = [&](int c) {
     const int k0 = c * KC;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int gk = k0 + ak + j;
-      ra[j] = zmake(0.0, 0.0);
-      if (gm < n && gk < n) ra[j] = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
-    }
-    if (has_b) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NV; ++j) {
+      rv[j] = zmake(0.0, 0.0);
+      if (is_a) {
+        const int gk = k0 + ak + j;
+        if (j < AK && gm < n && gk < n)
+          rv[j] = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+      } else {
         const int gk = k0 + bk + j;
-        rb[j] = zmake(0.0, 0.0);
-        if (gn < n && gk < n) rb[j] = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+        if (j < 4 && gn < n && gk < n)
+          rv[j] = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
       }
     }
   };
+  if (warp == 8) {
+    // ---------------- MMA warp: one elected lane issues, the others idle
+    if (lane == 0) {
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (!mbar_wait_cluster(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st_off = (uint32_t)(s * STAGE);
+        // descriptors of slice 0 at k-step 0; the others differ by compile-time address
+        // offsets, added to the start-address field (16-byte units, no carry out of it)
+        const uint64_t da = sdesc64(lbase + st_off), db = sdesc64(lbase + st_off + NS * A_SLICE);
+        const uint32_t first_chunk = (c == 0) ? 1u : 0u;
+#pragma unroll
+        for (int gsum = 0; gsum < NS; ++gsum) {        // scale group s + t
+#pragma unroll
+          for (int ps = 0; ps <= gsum; ++ps) {
+            const int pt = gsum - ps;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {           // K = 16 bf16 (32 bytes) per instruction
+              const uint32_t acc = (ps == 0 && ks == 0) ? (first_chunk ^ 1u) : 1u;
+              mma_bf16(tmem + (uint32_t)(gsum * NR),
+                       da + (uint64_t)((ps * A_SLICE + ks * 32) >> 4),
+                       db + (uint64_t)((pt * B_SLICE + ks * 32) >> 4), acc);
+            }
+          }
+        }
+        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+      }
+      mma_commit(done);
+    }
+  } else {
+  // ---------------- producer warps
   if (nchunks > 0) load(0);
-  bool ok = true;
   for (int c = 0; c < nchunks; ++c) {
     const int s = c & 1;
     if (c >= 2) {
-      if (tid == 0) s_wait_ok = mbar_wait(&bars[s], (uint32_t)(((c - 2) >> 1) & 1)) ? 1 : 0;
-      __syncthreads();
-      if (!s_wait_ok) { ok = false; break; }
+      // every member's MMAs of chunk c-2 must be done with stage s (a timed-out wait is
+      // recorded and the loop goes on)
+      if (!mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
     }
-    unsigned char* st = base + s * STAGE;
-    unsigned char* Asl = st;                       // NS planes of A_SLICE
-    unsigned char* Bsl = st + NS * A_SLICE;        // NS planes of B_SLICE
-    // this chunk's entries; the next chunk's loads are issued before digitizing
-    zc ca[8], cb[4];
+    const uint32_t st_off = (uint32_t)(s * STAGE);
+    unsigned char* Bsl = base + st_off + NS * A_SLICE;
+    zc cv[NV];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) ca[j] = ra[j];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) cb[j] = rb[j];
+    for (int j = 0; j < NV; ++j) cv[j] = rv[j];
     if (c + 1 < nchunks) load(c + 1);
-    // ---- A': real part -> columns ak..ak+7, imaginary part -> 16+ak..; 16-byte stores
-    {
-      unsigned int pr[NS][4], pi[NS][4];
+    unsigned int pr[NS][NV / 2], pi[NS][NV / 2];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        int dr[NS], di[NS];
-        digits(ca[j].x, ea_m, dr);
-        digits(ca[j].y, ea_m, di);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          if (j & 1) {
-            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
-            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
-          } else {
-            pr[q][j >> 1] = bf16_of_int(dr[q]);
-            pi[q][j >> 1] = bf16_of_int(di[q]);
-          }
-        }
-      }
-      const uint32_t o_r = sw64(am, ak), o_i = sw64(am, KC + ak);
+    for (int j = 0; j < NV; ++j) {
+      int dr[NS], di[NS];
+      digits(cv[j].x, escale, dr);
+      digits(cv[j].y, escale, di);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
-        *reinterpret_cast<uint4*>(Asl + q * A_SLICE + o_r) = make_uint4(pr[q][0], pr[q][1], pr[q][2], pr[q][3]);
-        *reinterpret_cast<uint4*>(Asl + q * A_SLICE + o_i) = make_uint4(pi[q][0], pi[q][1], pi[q][2], pi[q][3]);
+        if (j & 1) {
+          pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
+          pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+        } else {
+          pr[q][j >> 1] = bf16_of_int(dr[q]);
+          pi[q][j >> 1] = bf16_of_int(di[q]);
+        }
       }
     }
-    // ---- B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC+bn: [Im | Re]; 8-byte stores
-    if (has_b) {
-      unsigned int pr[NS][2], pi[NS][2];
+    if (is_a) {
+      // A': real part -> columns ak.., imaginary part -> KC+ak..; into every member
+      const uint32_t o_r = st_off + sw64(am, ak), o_i = st_off + sw64(am, KC + ak);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int dr[NS], di[NS];
-        digits(cb[j].x, eb_n, dr);
-        digits(cb[j].y, eb_n, di);
+      for (int q = 0; q < NS; ++q) {
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          if (j & 1) {
-            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
-            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+        for (int r = 0; r < CL; ++r) {
+          if (AK == 8) {
+            st_cluster_v4(rbase[r] + o_r + q * A_SLICE, pr[q][0], pr[q][1], pr[q][2], pr[q][3]);
+            st_cluster_v4(rbase[r] + o_i + q * A_SLICE, pi[q][0], pi[q][1], pi[q][2], pi[q][3]);
           } else {
-            pr[q][j >> 1] = bf16_of_int(dr[q]);
-            pi[q][j >> 1] = bf16_of_int(di[q]);
+            st_cluster_v2(rbase[r] + o_r + q * A_SLICE, pr[q][0], pr[q][1]);
+            st_cluster_v2(rbase[r] + o_i + q * A_SLICE, pi[q][0], pi[q][1]);
           }
         }
       }
+    } else {
+      // B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC+bn: [Im | Re]; local only
       const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
@@ -345,47 +446,23 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
         *reinterpret_cast<uint2*>(P + o4) = make_uint2(pr[q][0], pr[q][1]);
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // descriptors of slice 0 at k-step 0; the others differ by compile-time address
-      // offsets, added to the start-address field (16-byte units, no carry out of it)
-      const uint64_t da = sdesc64(smem_u32(Asl)), db = sdesc64(smem_u32(Bsl));
-      const uint32_t first_chunk = (c == 0) ? 1u : 0u;
+    // generic-proxy stores (local and remote) become visible to the tensor cores; one
+    // arrival per warp on every member's full[s]
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
 #pragma unroll
-      for (int gsum = 0; gsum < NS; ++gsum) {        // scale group s + t
-#pragma unroll
-        for (int ps = 0; ps <= gsum; ++ps) {
-          const int pt = gsum - ps;
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {           // K = 16 bf16 (32 bytes) per instruction
-            const uint32_t acc = (ps == 0 && ks == 0) ? (first_chunk ^ 1u) : 1u;
-            mma_bf16(tmem + (uint32_t)(gsum * NR),
-                     da + (uint64_t)((ps * A_SLICE + ks * 32) >> 4),
-                     db + (uint64_t)((pt * B_SLICE + ks * 32) >> 4), acc);
-          }
-        }
-      }
-      mma_commit(&bars[s]);
+      for (int r = 0; r < CL; ++r) mbar_arrive_remote(mapa_shared(smem_u32(&full[s]), (uint32_t)r));
     }
   }
-  if (tid == 0) {
-    if (ok && nchunks > 0) {
-      const int cl = nchunks - 1;
-      if (!mbar_wait(&bars[cl & 1], (uint32_t)((cl >> 1) & 1))) ok = false;
-    }
-    if (!ok) s_fail = 1;
+  // all MMAs of this member done (the MMA warp's last commit)
+  if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (s_fail) {
-    if (tid == 0) {
-      raise_error(err, NEGF_ERR_TIMEOUT);
-      if (nchunks > 0) mbar_wait(&bars[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1));
-    }
-    __syncthreads();
-  } else {
+    if (tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
+  } else if (warp < 8) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4)..; complex columns 16*(w/4) .. +15, 8 at a time
     const int q = warp & 3, h = warp >> 2;
     const int row = m0 + 32 * q + lane;
@@ -448,6 +525,332 @@ __global__ void __launch_bounds__(NT, 1) zgemm_oz_kernel(GemmArgs g, const int* 
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
+  cluster_sync();   // no member leaves while another may still address its shared memory
+}
+
+// ===========================================================================
+// Digitize-once variant.  oz_digitize_a writes the A operand's digits as pre-swizzled
+// shared-memory images in global memory ([unit][row tile][chunk][digit] planes, exactly
+// the stage layout of the MMA) with the row scale exponents; zgemm_ozt_kernel streams
+// them with bulk copies (each member copies 1/CL of a chunk's image and multicasts it
+// to the whole cluster), digitizes its own 32 B columns in four producer warps, and
+// issues the MMAs from one thread.
+// ===========================================================================
+constexpr uint32_t A_IMG = NS * A_SLICE;   // one chunk of one 128-row A tile (64 KB)
+constexpr uint32_t B_IMG = NS * B_SLICE;   // one chunk of one 32-column B tile (32 KB)
+
+struct OzImages {
+  unsigned char* a;   // [unit][tiles_m][nchunks] images of A_IMG bytes
+  int* ea;            // [unit][n] row scales of op(A)
+  int* eb;            // [unit][n] column scales of op(B)
+  int tiles_m, tiles_n, nchunks;
+};
+
+// A operand: one CTA per (32 rows, unit); each writes its rows of the 128-row tile images
+__global__ void __launch_bounds__(256) oz_digitize_a_kernel(GemmArgs g, OzImages im) {
+  const int u = blockIdx.y;
+  if (g.active && !g.active[u]) return;
+  constexpr int RB = 32;
+  const int n = g.n, r0 = blockIdx.x * RB, tm = r0 / TM;
+  const zc* A = g.A.at(u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int es[RB];
+  __shared__ double part[8][RB];
+  // ---- row scales of op(A): rows of A (op N, a warp per row) or columns of A (op H)
+  if (g.opA == OP_N) {
+    for (int r = warp; r < RB; r += 8) {
+      const int gm = r0 + r;
+      double v = 0.0;
+      if (gm < n)
+        for (int k = lane; k < n; k += 32) {
+          const zc x = A[(size_t)gm * n + k];
+          v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        }
+      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+      if (lane == 0) es[r] = scale_exp(v);
+    }
+  } else {
+    const int r = tid & 31, ks = tid >> 5, gm = r0 + r;
+    double v = 0.0;
+    if (gm < n)
+      for (int k = ks; k < n; k += 8) {
+        const zc x = A[(size_t)k * n + gm];
+        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+      }
+    part[ks][r] = v;
+    __syncthreads();
+    if (tid < RB) {
+      double w = 0.0;
+      for (int q = 0; q < 8; ++q) w = fmax(w, part[q][tid]);
+      es[tid] = scale_exp(w);
+    }
+  }
+  __syncthreads();
+  if (tid < RB && r0 + tid < n) im.ea[(size_t)u * n + r0 + tid] = es[tid];
+  // ---- digits: item (row, 2 consecutive complex k) per thread and chunk
+  const int rl = tid >> 3, ak = (tid & 7) * 2, gm = r0 + rl, am = gm - tm * TM;
+  const int e = es[rl];
+  for (int c = 0; c < im.nchunks; ++c) {
+    const int k0 = c * KC;
+    unsigned int pr[NS], pi[NS];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gk = k0 + ak + j;
+      zc v = zmake(0.0, 0.0);
+      if (gm < n && gk < n) v = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+      int dr[NS], di[NS];
+      digits(v.x, e, dr);
+      digits(v.y, e, di);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        if (j) {
+          pr[q] |= bf16_of_int(dr[q]) << 16;
+          pi[q] |= bf16_of_int(di[q]) << 16;
+        } else {
+          pr[q] = bf16_of_int(dr[q]);
+          pi[q] = bf16_of_int(di[q]);
+        }
+      }
+    }
+    unsigned char* img = im.a + ((size_t)(u * im.tiles_m + tm) * im.nchunks + c) * A_IMG;
+    const uint32_t o_r = sw64(am, ak), o_i = sw64(am, KC + ak);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      *reinterpret_cast<unsigned int*>(img + q * A_SLICE + o_r) = pr[q];
+      *reinterpret_cast<unsigned int*>(img + q * A_SLICE + o_i) = pi[q];
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bulk copy global -> this CTA's shared memory, completion counted on `bar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// bulk copy global -> the same shared offset of every member in `mask`, counted on each
+// member's barrier at the same offset
+__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                   uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+constexpr int NT_T = 192;   // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMAs
+
+template <int CL>
+__global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages im, int* err, int unit_alpha_beta) {
+  const int u = blockIdx.z;
+  if (g.active && !g.active[u]) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE);   // full[2], empty[2], done
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE + 48);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = g.n;
+  const int tm = blockIdx.y, tn = blockIdx.x;
+  const int m0 = tm * TM, n0 = tn * TNC;
+  const int nchunks = im.nchunks;
+
+  if (tid == 0) {
+    // full[s]: the A copy producer (expect_tx) and the four B producer warps
+    mbar_init(&full[0], 5);
+    mbar_init(&full[1], 5);
+    mbar_init(&empty[0], CL);
+    mbar_init(&empty[1], CL);
+    mbar_init(done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t rank = cluster_ctarank();
+  const uint32_t lbase = smem_u32(base);
+  const int* eB = im.eb + (size_t)u * n;
+  cluster_sync();   // every member's barriers are initialized before copies arrive
+
+  if (warp == 4) {
+    // ---------------- A: this member's 1/CL of the digit image, multicast to every member
+    if (lane == 0) {
+      const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks) * A_IMG;
+      constexpr uint32_t APART = A_IMG / CL;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+        const uint32_t st_off = (uint32_t)(s * STAGE);
+        mbar_expect_tx(&full[s], A_IMG);
+        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)c * A_IMG + rank * APART, APART, &full[s],
+                           (uint16_t)((1u << CL) - 1u));
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issue
+    if (lane == 0) {
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (!mbar_wait_cluster(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st_off = (uint32_t)(s * STAGE);
+        const uint64_t da = sdesc64(lbase + st_off), db = sdesc64(lbase + st_off + A_IMG);
+        const uint32_t first_chunk = (c == 0) ? 1u : 0u;
+#pragma unroll
+        for (int gsum = 0; gsum < NS; ++gsum) {
+#pragma unroll
+          for (int ps = 0; ps <= gsum; ++ps) {
+            const int pt = gsum - ps;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t acc = (ps == 0 && ks == 0) ? (first_chunk ^ 1u) : 1u;
+              mma_bf16(tmem + (uint32_t)(gsum * NR),
+                       da + (uint64_t)((ps * A_SLICE + ks * 32) >> 4),
+                       db + (uint64_t)((pt * B_SLICE + ks * 32) >> 4), acc);
+            }
+          }
+        }
+        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---------------- warps 0-3: B digits of column bn, 4 consecutive complex k from bk,
+    // straight from complex128 into this member's stage; then the epilogue
+    const int bn = tid >> 2, bk = (tid & 3) * 4, gn = n0 + bn;
+    const zc* B = g.B.at(u);
+    const int eb_n = (gn < n) ? eB[gn] : 0;
+    zc rb[4];
+    auto loadb = [&](int c) {
+      const int k0 = c * KC;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + bk + j;
+        rb[j] = zmake(0.0, 0.0);
+        if (gn < n && gk < n) rb[j] = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+      }
+    };
+    if (nchunks > 0) loadb(0);
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c & 1;
+      if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+      zc cb[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cb[j] = rb[j];
+      if (c + 1 < nchunks) loadb(c + 1);
+      unsigned int pr[NS][2], pi[NS][2];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int dr[NS], di[NS];
+        digits(cb[j].x, eb_n, dr);
+        digits(cb[j].y, eb_n, di);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (j & 1) {
+            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
+            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+          } else {
+            pr[q][j >> 1] = bf16_of_int(dr[q]);
+            pi[q][j >> 1] = bf16_of_int(di[q]);
+          }
+        }
+      }
+      unsigned char* Bsl = base + s * STAGE + A_IMG;
+      // B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC+bn: [Im | Re]
+      const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        unsigned char* P = Bsl + q * B_SLICE;
+        *reinterpret_cast<uint2*>(P + o1) = make_uint2(pr[q][0], pr[q][1]);
+        *reinterpret_cast<uint2*>(P + o2) = make_uint2(pi[q][0] ^ 0x80008000u, pi[q][1] ^ 0x80008000u);
+        *reinterpret_cast<uint2*>(P + o3) = make_uint2(pi[q][0], pi[q][1]);
+        *reinterpret_cast<uint2*>(P + o4) = make_uint2(pr[q][0], pr[q][1]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&full[s]);
+    }
+    // ---------------- epilogue: TMEM lanes 32*warp.., all 32 complex columns
+    if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    zc* D = g.D.at(u);
+    const zc* Cm = g.C.p ? g.C.at(u) : nullptr;
+    const int* eA = im.ea + (size_t)u * n;
+    const int er = (row < n) ? eA[row] : 0;
+#pragma unroll 1
+    for (int cc = 0; cc < TNC / 8; ++cc) {
+      const int j0 = 8 * cc;
+      long long hre[8], him[8], lre[8], lim[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) { hre[j] = 0; him[j] = 0; lre[j] = 0; lim[j] = 0; }
+#pragma unroll
+      for (int d = 0; d < NG; ++d) {
+        uint32_t vr[8], vi[8];
+        TC_LD8(lane_base + (uint32_t)(d * NR + j0), vr);
+        TC_LD8(lane_base + (uint32_t)(d * NR + TNC + j0), vi);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int sh = (d < HSPLIT) ? 7 * (HSPLIT - 1 - d) : 7 * (NG - 1 - d);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const long long gr = ((long long)__float2int_rn(__uint_as_float(vr[j]))) << sh;
+          const long long gi = ((long long)__float2int_rn(__uint_as_float(vi[j]))) << sh;
+          if (d < HSPLIT) { hre[j] += gr; him[j] += gi; }
+          else { lre[j] += gr; lim[j] += gi; }
+        }
+      }
+      if (row < n && !s_fail) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int gcol = n0 + j0 + j;
+          if (gcol < n) {
+            const int p = er + eB[gcol] - 7 * (NS + 1);
+            const int ph = p + 7 * (NG - HSPLIT);
+            zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
+                           ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            zc v;
+            if (unit_alpha_beta) {
+              v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
+              if (Cm && g.beta.x != 0.0) {
+                const zc cv = Cm[(size_t)row * n + gcol];
+                v = (g.beta.x > 0) ? zadd(v, cv) : zsub(v, cv);
+              }
+            } else {
+              v = zmul(g.alpha, acc);
+              if (Cm) v = zadd(v, zmul(g.beta, Cm[(size_t)row * n + gcol]));
+            }
+            D[(size_t)row * n + gcol] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_fail && tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+  cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
 
 }  // namespace
@@ -460,21 +863,99 @@ size_t oz_scratch_bytes(int n, int units) { return sizeof(int) * 2 * (size_t)n *
 cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  // cluster size: a tuning parameter (NEGF_OZ_CLUSTER = 2 or 4, default kCluster)
+  static int CL = 0;
+  if (CL == 0) {
+    const char* env = getenv("NEGF_OZ_CLUSTER");
+    CL = (env && atoi(env) == 2) ? 2 : kCluster;
+    cudaError_t e = cudaFuncSetAttribute(zgemm_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(zgemm_oz_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) { CL = 0; return e; }
   }
   int* ea = (int*)scratch;
   int* eb = ea + (size_t)g.n * g.units;
-  oz_scale_kernel<<<dim3(2, g.units), 256, 0, s>>>(g, ea, eb);
+  oz_scale_kernel<<<dim3(2, g.units), 256, 0, s>>>(g, ea, eb, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const bool unit_ab = (g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
-                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0)));
-  dim3 grid((g.n + TNC - 1) / TNC, (g.n + TM - 1) / TM, g.units);
-  zgemm_oz_kernel<<<grid, NT, SMEM_BYTES, s>>>(g, ea, eb, err, unit_ab ? 1 : 0);
+  const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
+                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
+                          ? 1 : 0;
+  const int tiles_n = (g.n + TNC - 1) / TNC;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((tiles_n + CL - 1) / CL * CL, (g.n + TM - 1) / TM, g.units);
+  cfg.blockDim = dim3(NT + 32, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (CL == 2) e = cudaLaunchKernelEx(&cfg, zgemm_oz_kernel<2>, g, (const int*)ea, (const int*)eb, err, unit_ab);
+  else e = cudaLaunchKernelEx(&cfg, zgemm_oz_kernel<4>, g, (const int*)ea, (const int*)eb, err, unit_ab);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// digitize-once variant: scales + A and B digit images
+static int ozt_tiles_n(int n) { return ((n + TNC - 1) / TNC + kCluster - 1) / kCluster * kCluster; }
+
+size_t ozt_scratch_bytes(int n, int units) {
+  const size_t nch = (size_t)(n + KC - 1) / KC;
+  const size_t tm = (size_t)(n + TM - 1) / TM;
+  size_t b = sizeof(int) * 2 * (size_t)n * units;
+  b = (b + 1023) & ~(size_t)1023;
+  b += (size_t)units * tm * nch * A_IMG;
+  return b;
+}
+
+cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  if (g.units <= 0 || g.n <= 0) return cudaSuccess;
+  if (!scratch) return cudaErrorInvalidValue;
+  constexpr int CL = kCluster;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(zgemm_ozt_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int n = g.n;
+  OzImages im;
+  im.nchunks = (n + KC - 1) / KC;
+  im.tiles_m = (n + TM - 1) / TM;
+  im.tiles_n = ozt_tiles_n(n);
+  unsigned char* p = (unsigned char*)scratch;
+  im.ea = (int*)p;
+  im.eb = im.ea + (size_t)n * g.units;
+  p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
+  im.a = p;
+  oz_digitize_a_kernel<<<dim3(im.tiles_m * (TM / 32), g.units), 256, 0, s>>>(g, im);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
+                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
+                          ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(im.tiles_n, im.tiles_m, g.units);
+  cfg.blockDim = dim3(NT_T, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, zgemm_ozt_kernel<CL>, g, im, err, unit_ab);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -253,7 +253,11 @@ struct Engine {
   cudaStream_t s;
   int mixed;           // 0: FP64, 1: digit-sliced BF16 tensor-core products, 2: TF32 3-term split
   void* inv_scratch;   // for inverses too large for shared memory
-  void* oz_scratch = nullptr;   // per-row/column scales of the sliced products
+  void* oz_scratch = nullptr;   // per-row/column scales of the sliced products (in-kernel digits)
+  void* ozt_scratch = nullptr;  // scales and digit images of the digitize-once sliced products
+  cudaError_t sliced(const GemmArgs& g) {
+    return ozt_scratch ? zgemm_ozt(g, ozt_scratch, ctx->d_err, s) : zgemm_oz(g, oz_scratch, ctx->d_err, s);
+  }
   // timing facility: events around one launch of class `cls`
   int open_cls = -1;
   cudaEvent_t open_ev = nullptr;
@@ -282,9 +286,9 @@ struct Engine {
     const double bytes = 16.0 * nn * units * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
     cudaError_t e;
     const bool masked = active != nullptr;   // masked launches do an unknown share of the work
-    if (mixed == 1 && oz_supported(n) && oz_scratch) {
+    if (mixed == 1 && oz_supported(n) && (oz_scratch || ozt_scratch)) {
       begin(masked ? K_OTHER : K_GEMM_OZ);
-      e = zgemm_oz(g, oz_scratch, ctx->d_err, s);
+      e = sliced(g);
     } else if (mixed == 2 && tc_supported(n)) {
       begin(masked ? K_OTHER : K_GEMM_TC);
       e = zgemm_tc(g, ctx->d_err, s);
@@ -318,9 +322,9 @@ struct Engine {
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
       r.n = n; r.units = units; r.active = nullptr;
       // M X with FP64-class accuracy: the sliced tensor-core product, else FP64 FMA
-      if (mixed == 1 && oz_supported(n) && oz_scratch) {
+      if (mixed == 1 && oz_supported(n) && (oz_scratch || ozt_scratch)) {
         begin(K_GEMM_OZ);
-        e = zgemm_oz(r, oz_scratch, ctx->d_err, s);
+        e = sliced(r);
       } else {
         begin(K_GEMM_F64);
         e = zgemm_f64(r, s);
@@ -380,7 +384,8 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     eng.inv_scratch = (void*)p;
     p += zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0);
   }
-  eng.oz_scratch = (void*)p;
+  p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+  eng.ozt_scratch = (void*)p;
 
   auto S1 = [&](zc* base) { return BMat{base, bb}; };
   // per-energy output blocks: [e][i] with unit stride nb*b*b (diag) or (nb-1)*b*b (off-diagonal)
@@ -469,7 +474,7 @@ size_t rgf_bytes_per_energy(int nb, int b, const RgfIO& io, int mixed) {
   if (!io.GRu) n += 1;
   size_t bytes = n * blk;
   bytes += zinv_scratch_bytes(b, 1, mixed ? 1 : 0);
-  bytes += oz_scratch_bytes(b, 1);
+  if (mixed == 1) bytes += ozt_scratch_bytes(b, 1) + 1024;
   return bytes;
 }
 
@@ -1281,7 +1286,8 @@ negf_status negf_block_gemm(negf_ctx* c, negf_precision prec, int32_t n, int32_t
   CU(cudaSetDevice(ctx->device));
   Engine eng{ctx, (cudaStream_t)stream, (int)prec, nullptr};
   if (oz_scratch_bytes(n, units) > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small");
-  eng.oz_scratch = ctx->ws;
+  if (ozt_scratch_bytes(n, units) <= ctx->ws_bytes) eng.ozt_scratch = ctx->ws;
+  else eng.oz_scratch = ctx->ws;
   CU(eng.gemm(BMat{(zc*)D, d_stride}, BMat{(zc*)A, a_stride}, opA, BMat{(zc*)B, b_stride}, opB,
               zmake(alpha[0], alpha[1]), C ? BMat{(zc*)C, c_stride} : NOMAT,
               C ? zmake(beta[0], beta[1]) : ZERO, n, units));
@@ -1310,6 +1316,10 @@ negf_status negf_block_inverse(negf_ctx* c, negf_precision prec, int32_t n, int3
   BMat T1{ws, bb}, T2{ws + (mixed ? units * bb : 0), bb};
   eng.inv_scratch = (void*)(ws + (mixed ? 2 * units * bb : 0));
   eng.oz_scratch = (char*)eng.inv_scratch + inv_b;
+  {
+    char* q = (char*)(((uintptr_t)eng.oz_scratch + 1023) & ~(uintptr_t)1023);
+    if ((size_t)(q - (char*)ctx->ws) + ozt_scratch_bytes(n, units) <= ctx->ws_bytes) eng.ozt_scratch = q;
+  }
   if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * units, s));
   CU(eng.inverse(BMat{(zc*)X, bb}, BMat{(zc*)M, bb}, n, units, status, T1, T2));
   return NEGF_OK;

@@ -106,6 +106,10 @@ bool tc_supported(int n);
 cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 bool oz_supported(int n);
 size_t oz_scratch_bytes(int n, int units);
+// the same product with each operand digitized once into global memory and streamed to
+// the tensor cores by bulk copies; `scratch` holds ozt_scratch_bytes(n, units) bytes
+cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
+size_t ozt_scratch_bytes(int n, int units);
 
 // X[u] = M[u]^{-1} by Gauss-Jordan with partial pivoting (first max |.| in row
 // order).  FP64, or FP32 (`single` != 0) with the result written back in FP64.
