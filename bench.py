@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
+# BF16 slice-pair products per complex product in the sliced GEMM (8 digits, s + t <= 9)
+OZ_SLICE_PAIRS = 36.0
+
 METRIC = ("energy points/sec (G^R+G^< RGF, nb=64, bs=128) mixed vs FP64 on 1 GB300 at ≤1e-6 rel")
 UNIT = "energy points/s"
 
@@ -146,12 +149,13 @@ def roofline_for(cls, stats, peaks, peak_src, sustained=True):
     achieved = (fl / n) / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
     bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
     if cls == "gemm_oz":
-        # 7-digit slicing: 28 BF16 slice-pair products per complex product (n = 128 tiles
-        # exactly); tensor flops = 28 x the 8 n^3 useful flops, against the BF16 peak
-        achieved *= 28.0
+        # 8-digit slicing: 36 BF16 slice-pair products (s + t <= 9) per complex product
+        # (n = 128 tiles exactly); tensor flops = 36 x the 8 n^3 useful flops, against
+        # the BF16 peak
+        achieved *= OZ_SLICE_PAIRS
         bound, peak, unit = "tensor", bf16, "TFLOP/s"
-        note = (f"BF16 tensor flops executed (28 x useful) vs bf16 {'sustained' if sustained else 'burst'} "
-                f"{peak_src} peak")
+        note = (f"BF16 tensor flops executed ({OZ_SLICE_PAIRS:.0f} x useful) vs bf16 "
+                f"{'sustained' if sustained else 'burst'} {peak_src} peak")
     elif cls == "gemm_tc":
         bound, peak, unit = "tensor", bf16 * (1.1 / 2.25) / 3.0, "TFLOP/s"
         note = f"useful complex flops vs TF32 peak/3 (TF32 = bf16 {peak_src} x 1.1/2.25)"
@@ -446,7 +450,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {P.MIXED: "bf16 7-digit slices (exact fp32 accumulate) + f32 inverse + f64",
+        "dtype": {P.MIXED: "bf16 8-digit slices (exact fp32 accumulate) + f32 inverse + f64",
                   P.MIXED_TF32: "tf32x3 + f32 inverse + f64", P.FP64: "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": f"config 2: ballistic batched RGF, nb={nb}, b={b}, {ne} energies/GPU in [-3,3], "

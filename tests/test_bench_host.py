@@ -86,4 +86,4 @@ def test_roofline_sliced_gemm_counts_tensor_work():
     r = bench.roofline_for("gemm_oz", st, peaks, "measured")
     useful = 8 * 128 ** 3 * 100.0 / 2e-3 / 1e12
     assert abs(r["useful_tflops"] - useful) < 1e-9
-    assert abs(r["achieved"] - 28 * useful) < 1e-9 and r["peak"] == 1650.0
+    assert abs(r["achieved"] - 36 * useful) < 1e-9 and r["peak"] == 1650.0
