@@ -33,7 +33,8 @@ __all__ = [
     "dense_matrix", "dense_H_S", "lead_A_blocks", "sancho_rubio", "surface_residual",
     "lead_self_energies", "lead_lesser", "gamma", "assemble_A", "assemble_sigma_lesser",
     "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
-    "interface_current", "density", "solve_energy",
+    "interface_current", "density", "solve_energy", "retarded_check", "surface_newton_warm",
+    "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf",
 ]
 
 
@@ -196,6 +197,70 @@ def surface_gf(a00, alpha, beta, tol=1e-12, max_iter=100, target=1e-13, newton_s
     g, it, ok = sancho_rubio(a00, alpha, beta, tol, max_iter)
     g, ns, res = surface_newton(a00, alpha, beta, g, target, newton_steps)
     return g, it, ns, res, ok
+
+
+def retarded_check(g, tol=1e-12):
+    """Is ``g`` the retarded (decaying) root of the surface equation?
+
+    For a lead with S = I, every root of g = (a00 - alpha g beta)^{-1} satisfies the
+    Stein equation  A = 2 eta g g^H + (g H01) A (g H01)^H  for A = i (g - g^H), whose
+    constant term is positive definite for eta > 0.  By the inertia theorem for Stein
+    equations, A is then positive definite exactly when rho(g H01) < 1, i.e. when g is
+    built from the decaying (retarded) modes; the other roots solve the same quadratic
+    equation to the same residual but leave A indefinite.  The test is the LDL^H
+    factorisation of A without pivoting (Sylvester's criterion): every pivot must
+    exceed -tol * max_k A_kk; a pivot within +-tol of zero is taken as a semidefinite
+    direction and its column skipped."""
+    A = 1j * (g - g.conj().T)
+    A = 0.5 * (A + A.conj().T)
+    n = A.shape[0]
+    scale = max(float(np.max(A.real.diagonal())), 1e-300)
+    W = A.copy()
+    for k in range(n):
+        d = W[k, k].real
+        if d < -tol * scale or not np.isfinite(d):
+            return False
+        if d <= tol * scale:
+            continue
+        l = W[k + 1:, k] / d
+        W[k + 1:, k + 1:] -= np.outer(l, W[k, k + 1:])
+    return True
+
+
+def surface_newton_warm(a00, alpha, beta, g0, target=1e-13, max_steps=8, smith_levels=96):
+    """Guess-driven surface solver: plain Newton steps on F(X) = (a00 - alpha X beta) X - I
+    from the initial guess ``g0`` (every finite step is taken; the Stein equation of each
+    step is summed by Smith doubling with at most ``smith_levels`` levels).
+    Returns (X, steps, residual); the residual is inf when a step did not stay finite."""
+    b = a00.shape[0]
+    X = g0
+    res = surface_residual(a00, alpha, beta, X)
+    steps = 0
+    while res > target and steps < max_steps:
+        K = a00 - alpha @ X @ beta
+        F = K @ X - np.eye(b)
+        Kinv = np.linalg.inv(K)
+        with np.errstate(all="ignore"):
+            D = stein_smith(Kinv @ alpha, beta @ X, -(Kinv @ F), max_iter=smith_levels)
+            X = X + D
+            res = surface_residual(a00, alpha, beta, X)
+        steps += 1
+        if not np.isfinite(res):
+            return X, steps, np.inf
+    return X, steps, res
+
+
+def warm_surface_gf(a00, alpha, beta, g0, accept=1e-10, tol=1e-12, max_iter=100, target=1e-13,
+                    warm_steps=8):
+    """Surface function from a warm start, with the decimation as fallback and judge:
+    Newton from ``g0``; the result is taken when its residual is <= ``accept`` and it
+    passes ``retarded_check``; otherwise the plain decimation + polishing runs.
+    Returns (g, decimation iterations, newton steps, residual, warm_taken)."""
+    X, steps, res = surface_newton_warm(a00, alpha, beta, g0, target, warm_steps)
+    if res <= accept and retarded_check(X):
+        return X, 0, steps, res, True
+    g, it, ns, r, ok = surface_gf(a00, alpha, beta, tol, max_iter, target)
+    return g, it, ns, r, False
 
 
 def lead_self_energies(dev, z, tol=1e-12, max_iter=100, newton_steps=3):
