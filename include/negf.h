@@ -130,14 +130,30 @@ negf_status negf_layout(const negf_system* sys, int64_t* out);
  * Newton steps on the surface fixed-point equation; an energy whose surface
  * residual ||(a00 - a01 g a10) g - I||_F / sqrt(b) stays above 1e-10 gets
  * NEGF_ERR_NOCONV in status[e].  Sigma_L = a10 g_L a01, Sigma_R = a01 g_R a10.
- *   g0_L, g0_R : reserved for a warm start, must be NULL.
+ *
+ * Warm start (optional, per lead side): with g0_L and/or g0_R given, that side
+ * first takes up to 8 plain Newton steps from the guess (each step's Stein
+ * equation summed by Smith doubling, at most 96 levels).  The Newton result is
+ * kept when its residual is <= 1e-10 and it passes the retarded-root test: the
+ * LDL^H pivots of A = i (g - g^H) all exceed -1e-12 max_k A_kk (for S = I leads
+ * A is positive definite exactly for the decaying root, by the inertia theorem
+ * of the Stein equation A = 2 eta g g^H + (g H01) A (g H01)^H).  Otherwise that
+ * lead of that energy falls back to the decimation above, which stays the judge
+ * of the 1e-10 residual.  The guesses have no counterpart in the paper; see
+ * negf_warmstart.h for the network that produces them.
+ *   g0_L, g0_R : in, device [sum ne] blocks of surface-function guesses, or NULL.
  *   sigma_L/R  : out, device [sum ne] blocks.
- *   iters      : out, device int32 [2*sum ne]: decimation steps (L, R) per energy, or NULL.
+ *   gs_L, gs_R : out, device [sum ne] blocks: the surface functions g_L, g_R, or NULL.
+ *   iters      : out, device int32 [2*sum ne]: decimation steps (L, R) per energy
+ *                (0 when the warm start was kept), or NULL.
+ *   newton     : out, device int32 [2*sum ne]: Newton steps (L, R) per energy, warm
+ *                and polishing steps together, or NULL.
  *   status     : out, device int32 [sum ne] (NEGF_OK or a negative code), or NULL.
  * Requires nb >= 2 for every device. */
 negf_status negf_obc(negf_ctx* ctx, const negf_system* sys, double tol, int32_t max_iter,
                      const void* g0_L, const void* g0_R, void* sigma_L, void* sigma_R,
-                     int32_t* iters, int32_t* status, negf_stream stream);
+                     void* gs_L, void* gs_R, int32_t* iters, int32_t* newton, int32_t* status,
+                     negf_stream stream);
 
 /* Selected blocks of G^R (Eq. (1)) by the forward/backward recursive Green's
  * function sweeps (RGF, Sec. II).  sigma_L/R from negf_obc (or any retarded

@@ -11,8 +11,11 @@ guess-driven open-boundary solver.  What it computes, in plain numpy float64:
                  | sqrt(b) Im H00[i,j], i < j        (b(b-1)/2)
                  | sqrt(b) Re H01                    (b^2, row-major)
                  | sqrt(b) Im H01                    (b^2)
-                 | E / 3 ]                           -> K0 = 3 b^2 + 1 values,
-             zero-padded to K0P (a multiple of 128);
+                 | E / 3
+                 | sin(w_m E), cos(w_m E), m = 0..31 ]  -> K0 = 3 b^2 + 65 values,
+             zero-padded to K0P (a multiple of 128); w_m = 2^(m/4), written as
+             2^(m div 4) times 2^((m mod 4)/4) so that both sides form the same double
+             (a Fourier encoding of the energy, finer than one BF16 feature resolves);
   network    z1 = W1 x + c1,  h1 = relu(z1)           (hidden)
              z2 = W2 h1 + c2, h2 = relu(z2)           (hidden)
              y  = W3 h2 + c3                          (2 b^2)
@@ -36,6 +39,13 @@ __all__ = ["bf16_round", "mlp_dims", "param_layout", "split_params", "pack_featu
            "unpack_output", "forward", "loss_and_grads", "adam_step"]
 
 E_SCALE = 1.0 / 3.0
+N_FREQ = 32
+_ROOTS2 = (1.0, 1.189207115002721, 1.4142135623730951, 1.6817928305074290)   # 2^(k/4), k = 0..3
+
+
+def freqs():
+    """w_m = 2^(m/4), m = 0..N_FREQ-1, as 2^(m div 4) * 2^((m mod 4)/4)."""
+    return np.array([np.ldexp(_ROOTS2[m & 3], m >> 2) for m in range(N_FREQ)])
 
 
 def bf16_round(x):
@@ -48,7 +58,7 @@ def bf16_round(x):
 
 def mlp_dims(b, hidden=512):
     """(K0, K0P, hidden, NOUT): feature count, padded feature count, width, outputs."""
-    k0 = 3 * b * b + 1
+    k0 = 3 * b * b + 1 + 2 * N_FREQ
     k0p = (k0 + 127) // 128 * 128
     return k0, k0p, hidden, 2 * b * b
 
@@ -82,16 +92,20 @@ def pack_features(H00, H01, E):
     parts = [H00.real[np.arange(b), np.arange(b)], H00.real[iu], H00.imag[iu],
              H01.real.reshape(-1), H01.imag.reshape(-1)]
     x = np.zeros(k0p)
-    x[:k0 - 1] = np.concatenate(parts) * s
-    x[k0 - 1] = E * E_SCALE
+    nh = 3 * b * b
+    x[:nh] = np.concatenate(parts) * s
+    x[nh] = E * E_SCALE
+    w = freqs() * E
+    x[nh + 1:nh + 1 + 2 * N_FREQ:2] = np.sin(w)
+    x[nh + 2:nh + 2 + 2 * N_FREQ:2] = np.cos(w)
     return x
 
 
 def unpack_features(x, b):
     """Inverse of the packing (for the pins): (H00, H01, E)."""
     s = np.sqrt(float(b))
-    k0 = 3 * b * b + 1
-    v = x[:k0 - 1] / s
+    nh = 3 * b * b
+    v = x[:nh] / s
     nu = b * (b - 1) // 2
     d, re, im = v[:b], v[b:b + nu], v[b + nu:b + 2 * nu]
     H00 = np.zeros((b, b), dtype=np.complex128)
@@ -101,7 +115,7 @@ def unpack_features(x, b):
     H00[np.arange(b), np.arange(b)] = d
     r = v[b + 2 * nu:]
     H01 = (r[:b * b] + 1j * r[b * b:]).reshape(b, b)
-    return H00, H01, x[k0 - 1] / E_SCALE
+    return H00, H01, x[nh] / E_SCALE
 
 
 def pack_target(g):

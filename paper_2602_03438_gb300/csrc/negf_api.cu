@@ -519,9 +519,18 @@ __global__ void lead_init_kernel(LeadArgs a) {
 
 // per unit: m = max(max|al|, max|be|).  mode 0: ref[u] = m.  mode 1: convergence check.
 __global__ void lead_norm_kernel(BMat al, BMat be, int n, int mode, double* ref, int* done, int* live, int* iters,
-                                 int it, double tol, int* n_active) {
+                                 int it, double tol, int* n_active, const int* skip = nullptr) {
   const int u = blockIdx.x;
   if (mode == 1 && done[u]) return;
+  if (mode == 0 && skip && skip[u]) {   // solved by the warm start: no decimation
+    if (threadIdx.x == 0) {
+      ref[u] = 1.0;
+      done[u] = 1;
+      live[u] = 0;
+      iters[u] = 0;
+    }
+    return;
+  }
   const long long nn = (long long)n * n;
   const zc* x = al.at(u);
   const zc* y = be.at(u);
@@ -649,7 +658,7 @@ __global__ void balance_kernel(BMat P, BMat Q, int n, const int* act) {
 
 // Newton acceptance: if resn < res: g = gn, res = resn
 __global__ void newton_accept_kernel(BMat g, BMat gn, int n, double* res, const double* resn, int* need,
-                                     double target) {
+                                     double target, int* steps) {
   const int u = blockIdx.x;
   if (!need[u]) return;
   const bool take = resn[u] < res[u];
@@ -661,7 +670,107 @@ __global__ void newton_accept_kernel(BMat g, BMat gn, int n, double* res, const 
   if (threadIdx.x == 0) {
     if (take) res[u] = resn[u];
     need[u] = (take && res[u] > target) ? 1 : 0;
+    ++steps[u];
   }
+}
+
+// warm-start Newton: every finite step is taken; a non-finite one ends the unit's
+// attempt (res = inf, so that the retarded-root test rejects it)
+__global__ void newton_take_kernel(BMat g, BMat gn, int n, double* res, const double* resn, int* need,
+                                   double target, int* steps) {
+  const int u = blockIdx.x;
+  if (!need[u]) return;
+  const bool fin = isfinite(resn[u]);
+  if (fin) {
+    const long long nn = (long long)n * n;
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) g.at(u)[i] = gn.at(u)[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++steps[u];
+    if (fin) {
+      res[u] = resn[u];
+      need[u] = res[u] > target ? 1 : 0;
+    } else {
+      res[u] = INFINITY;
+      need[u] = 0;
+    }
+  }
+}
+
+// g[u] = the guess of its side (left units u < U, right units u >= U), warm[u] = 1 when given
+__global__ void guess_init_kernel(BMat g, const zc* g0L, const zc* g0R, int U, int n, int* warm) {
+  const int u = blockIdx.y;
+  const bool left = u < U;
+  const zc* src = left ? g0L : g0R;
+  if (blockIdx.x == 0 && threadIdx.x == 0) warm[u] = src ? 1 : 0;
+  if (!src) return;
+  const long long nn = (long long)n * n;
+  src += (long long)(left ? u : u - U) * nn;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+    g.at(u)[i] = src[i];
+}
+
+__global__ void need_warm_kernel(const int* warm, const double* res, int* need, int units, double target) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < units) need[u] = (warm[u] && res[u] > target) ? 1 : 0;
+}
+
+// retarded-root test of the warm result: keep[u] = 1 when the unit had a guess, its
+// residual is <= accept, and every LDL^H pivot (no pivoting) of A = i (g - g^H) exceeds
+// -tol * max_k A_kk (a pivot within +-tol of zero is a semidefinite direction and is
+// skipped).  A is factorised in place in the scratch block W.
+__global__ void retarded_check_kernel(BMat g, BMat W, int n, const int* warm, const double* res, double accept,
+                                      double tol, int* keep) {
+  const int u = blockIdx.x;
+  if (!warm[u] || !(res[u] <= accept)) {
+    if (threadIdx.x == 0) keep[u] = 0;
+    return;
+  }
+  const long long nn = (long long)n * n;
+  const zc* x = g.at(u);
+  zc* A = W.at(u);
+  double mx = 0.0;
+  for (long long idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+    const zc a = x[idx], c = x[(long long)j * n + i];
+    // A_ij = i (g_ij - conj(g_ji))
+    A[idx] = zmake(-(a.y + c.y), a.x - c.x);
+    if (i == j) mx = fmax(mx, -2.0 * a.y);
+  }
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  __shared__ double s_scale;
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    s_scale = fmax(mx, 1e-300);
+  }
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const double d = A[(long long)k * n + k].x;
+    if (d < -tol * s_scale || !isfinite(d)) {
+      if (threadIdx.x == 0) keep[u] = 0;
+      return;
+    }
+    if (d <= tol * s_scale) continue;
+    const int m = n - k - 1;
+    const double inv = 1.0 / d;
+    for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) {
+      const int i = k + 1 + (int)(idx / m), j = k + 1 + (int)(idx % m);
+      const zc l = A[(long long)i * n + k], r = A[(long long)k * n + j];
+      zc& t = A[(long long)i * n + j];
+      t.x -= (l.x * r.x - l.y * r.y) * inv;
+      t.y -= (l.x * r.y + l.y * r.x) * inv;
+    }
+  }
+  if (threadIdx.x == 0) keep[u] = 1;
+}
+
+__global__ void not_kernel(const int* a, int* out, int units) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < units) out[u] = a[u] ? 0 : 1;
 }
 
 __global__ void count_kernel(const int* flags, int units, int* out) {
@@ -677,13 +786,13 @@ __global__ void count_kernel(const int* flags, int units, int* out) {
   }
 }
 
-__global__ void set_need_kernel(const double* res, int* need, int units, double target) {
+__global__ void set_need_kernel(const double* res, int* need, int units, double target, const int* only) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < units) need[u] = res[u] > target ? 1 : 0;
+  if (u < units) need[u] = (only[u] && res[u] > target) ? 1 : 0;
 }
 
-__global__ void obc_finish_kernel(const int* done, const double* res, const int* iters, int U, int32_t* status,
-                                  int32_t* iters_out, double accept) {
+__global__ void obc_finish_kernel(const int* done, const double* res, const int* iters, const int* nsteps, int U,
+                                  int32_t* status, int32_t* iters_out, int32_t* newton_out, double accept) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= U) return;
   const bool okL = done[e] == 1 && res[e] <= accept;
@@ -692,6 +801,10 @@ __global__ void obc_finish_kernel(const int* done, const double* res, const int*
   if (iters_out) {
     iters_out[2 * e] = iters[e];
     iters_out[2 * e + 1] = iters[U + e];
+  }
+  if (newton_out) {
+    newton_out[2 * e] = nsteps[e];
+    newton_out[2 * e + 1] = nsteps[U + e];
   }
 }
 
@@ -993,15 +1106,14 @@ negf_status negf_rgf_lesser(negf_ctx* c, const negf_system* sys, negf_precision 
 
 // ---------------------------------------------------------------------------
 negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t max_iter, const void* g0_L,
-                     const void* g0_R, void* sigma_L, void* sigma_R, int32_t* iters, int32_t* status,
-                     negf_stream stream) {
+                     const void* g0_R, void* sigma_L, void* sigma_R, void* gs_L, void* gs_R, int32_t* iters,
+                     int32_t* newton, int32_t* status, negf_stream stream) {
   Ctx* ctx = reinterpret_cast<Ctx*>(c);
   if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
   Layout L;
   negf_status st = make_layout(ctx, sys, L);
   if (st != NEGF_OK) return st;
   if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
-  if (g0_L || g0_R) return fail(ctx, NEGF_ERR_ARG, "warm start pointers must be NULL");
   if (!sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "sigma_L and sigma_R outputs are required");
   if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000)
     return fail(ctx, NEGF_ERR_ARG, "need tol > 0 and 1 <= max_iter <= 1000");
@@ -1010,8 +1122,9 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
   CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Engine eng{ctx, s, 0, nullptr};
-  const double target = 1e-13;   // Newton polishing target
+  const double target = 1e-13;   // Newton target
   const double accept = 1e-10;   // success threshold of the surface residual
+  const bool any_warm = g0_L || g0_R;
   for (int d = 0; d < sys->ndev; ++d) {
     const int ne = sys->ne[d];
     if (ne == 0) continue;
@@ -1041,6 +1154,10 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       int* it_arr = (int*)p; p += sizeof(int) * NU;
       int* need = (int*)p; p += sizeof(int) * NU;
       int* act = (int*)p; p += sizeof(int) * NU;
+      int* warm = (int*)p; p += sizeof(int) * NU;     // unit has a guess
+      int* keep = (int*)p; p += sizeof(int) * NU;     // warm result kept
+      int* cold = (int*)p; p += sizeof(int) * NU;     // unit goes through the decimation
+      int* nsteps = (int*)p; p += sizeof(int) * NU;   // Newton steps taken
       int* n_active = (int*)p; p += 16;
       p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
       eng.inv_scratch = zinv_scratch_bytes(b, NU, 0) ? (void*)p : nullptr;
@@ -1049,35 +1166,9 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), NU);
       lead_init_kernel<<<eg, 256, 0, s>>>(la);
       KCHECK();
-      lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 0, ref, done, act, it_arr, 0, tol, n_active);
-      KCHECK();
-      // ---- decimation
-      for (int it = 0; it <= max_iter; ++it) {
-        const bool poll = (it & 3) == 3 || it == max_iter;
-        if (poll) CU(cudaMemsetAsync(n_active, 0, sizeof(int), s));
-        lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 1, ref, done, act, it_arr, it, tol,
-                                            poll ? n_active : nullptr);
-        KCHECK();
-        if (poll) {
-          CU(cudaMemcpyAsync(ctx->h_pinned, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-          CU(cudaStreamSynchronize(s));
-          if (ctx->h_pinned[0] == 0) break;
-        }
-        if (it == max_iter) break;
-        CU(eng.inv(g, eps, b, NU, act, 0, nullptr));                     // g = eps^{-1}
-        CU(eng.gemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // al g
-        CU(eng.gemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // be g
-        CU(eng.gemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // al g be
-        CU(eng.gemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // be g al
-        lead_update_kernel<<<eg, 256, 0, s>>>(eps, epss, T[2], T[3], b, done);
-        KCHECK();
-        CU(eng.gemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -al g al
-        CU(eng.gemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -be g be
-        std::swap(al, T[4]);
-        std::swap(be, T[5]);
-      }
-      // ---- surface function and its residual
-      CU(eng.inv(g, epss, b, NU, nullptr, 0, nullptr));
+      CU(cudaMemsetAsync(nsteps, 0, sizeof(int) * NU, s));
+      CU(cudaMemsetAsync(keep, 0, sizeof(int) * NU, s));
+
       auto residual = [&](BMat X, double* out, const int* mask) -> negf_status {
         CU(eng.gemm(T[0], al0, OP_N, X, OP_N, ONE, NOMAT, ZERO, b, NU, mask));               // al X
         CU(eng.gemm(T[1], T[0], OP_N, be0, OP_N, MONE, a00, ONE, b, NU, mask));              // K = a00 - al X be
@@ -1094,23 +1185,16 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e == cudaSuccess ? ctx->h_pinned[0] : -1;
       };
-      if ((st = residual(g, res, nullptr)) != NEGF_OK) return st;
-      // ---- Newton polishing of the fixed point g = (a00 - al g be)^{-1}:
+      // One Newton step on F(X) = (a00 - al X be) X - I for the units flagged in `mask`:
       // K D - al D (be g) = -F, solved as the Stein equation D = -K^{-1}F + (K^{-1} al) D (be g)
-      // by Smith doubling, for the units whose residual is above the target
-      set_need_kernel<<<(NU + 255) / 256, 256, 0, s>>>(res, need, NU, target);
-      KCHECK();
-      BMat gn = eps;   // decimation slots are free now
-      for (int step = 0; step < 3; ++step) {
-        int cnt = n_set(need);
-        if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
-        if (cnt == 0) break;
-        // T1 = K and T2 = F of the current g (left there by the last residual evaluation)
-        CU(eng.inv(T[3], T[1], b, NU, need, 0, nullptr));                 // K^{-1}
-        CU(eng.gemm(T[4], T[3], OP_N, al0, OP_N, ONE, NOMAT, ZERO, b, NU, need));          // P = K^{-1} al
-        CU(eng.gemm(T[5], be0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, need));             // Q = be g
-        CU(eng.gemm(T[6], T[3], OP_N, T[2], OP_N, MONE, NOMAT, ZERO, b, NU, need));        // S = -K^{-1} F
-        CU(cudaMemcpyAsync(act, need, sizeof(int) * NU, cudaMemcpyDeviceToDevice, s));
+      // by Smith doubling (at most 96 levels); gn = g + D and resn = its residual.
+      // T1 = K and T2 = F of the current g must be in place (left by the last residual).
+      auto newton_step = [&](int* mask, BMat gn) -> negf_status {
+        CU(eng.inv(T[3], T[1], b, NU, mask, 0, nullptr));                 // K^{-1}
+        CU(eng.gemm(T[4], T[3], OP_N, al0, OP_N, ONE, NOMAT, ZERO, b, NU, mask));          // P = K^{-1} al
+        CU(eng.gemm(T[5], be0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, mask));             // Q = be g
+        CU(eng.gemm(T[6], T[3], OP_N, T[2], OP_N, MONE, NOMAT, ZERO, b, NU, mask));        // S = -K^{-1} F
+        CU(cudaMemcpyAsync(act, mask, sizeof(int) * NU, cudaMemcpyDeviceToDevice, s));
         BMat Pm = T[4], Qm = T[5], Sm = T[6], W1 = T[0], W2 = T[2], W3 = T[3];
         for (int j = 0; j < 96; ++j) {
           CU(eng.gemm(W1, Pm, OP_N, Sm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P S
@@ -1124,18 +1208,93 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
           balance_kernel<<<NU, 256, 0, s>>>(Pm, Qm, b, act);
           KCHECK();
           if ((j & 7) == 7) {
-            cnt = n_set(act);
+            const int cnt = n_set(act);
             if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
             if (cnt == 0) break;
           }
         }
-        add_kernel<<<eg, 256, 0, s>>>(gn, g, Sm, b, need);                                  // g + D
+        add_kernel<<<eg, 256, 0, s>>>(gn, g, Sm, b, mask);                                  // g + D
         KCHECK();
-        if ((st = residual(gn, resn, need)) != NEGF_OK) return st;
-        newton_accept_kernel<<<NU, 256, 0, s>>>(g, gn, b, res, resn, need, target);
+        return residual(gn, resn, mask);
+      };
+
+      // ---- warm start: Newton from the guesses, kept only if converged and retarded
+      if (any_warm) {
+        const zc* gl = g0_L ? (const zc*)g0_L + o[3] + (long long)e0 * bb : nullptr;
+        const zc* gr = g0_R ? (const zc*)g0_R + o[3] + (long long)e0 * bb : nullptr;
+        guess_init_kernel<<<eg, 256, 0, s>>>(g, gl, gr, U, b, warm);
         KCHECK();
-        // units that took the step continue from T1/T2 (K, F of the accepted g)
+        if ((st = residual(g, res, warm)) != NEGF_OK) return st;
+        need_warm_kernel<<<(NU + 255) / 256, 256, 0, s>>>(warm, res, need, NU, target);
+        KCHECK();
+        for (int step = 0; step < 8; ++step) {
+          const int cnt = n_set(need);
+          if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
+          if (cnt == 0) break;
+          if ((st = newton_step(need, eps)) != NEGF_OK) return st;   // eps is free until the decimation
+          newton_take_kernel<<<NU, 256, 0, s>>>(g, eps, b, res, resn, need, target, nsteps);
+          KCHECK();
+        }
+        retarded_check_kernel<<<NU, 256, 0, s>>>(g, T[0], b, warm, res, accept, 1e-12, keep);
+        KCHECK();
+        lead_init_kernel<<<eg, 256, 0, s>>>(la);   // restore the decimation slots
+        KCHECK();
       }
+      not_kernel<<<(NU + 255) / 256, 256, 0, s>>>(keep, cold, NU);
+      KCHECK();
+      const int n_cold = any_warm ? n_set(cold) : NU;
+      if (n_cold < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
+
+      lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 0, ref, done, act, it_arr, 0, tol, n_active, keep);
+      KCHECK();
+      if (n_cold > 0) {
+        // ---- decimation
+        for (int it = 0; it <= max_iter; ++it) {
+          const bool poll = (it & 3) == 3 || it == max_iter;
+          if (poll) CU(cudaMemsetAsync(n_active, 0, sizeof(int), s));
+          lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 1, ref, done, act, it_arr, it, tol,
+                                              poll ? n_active : nullptr);
+          KCHECK();
+          if (poll) {
+            CU(cudaMemcpyAsync(ctx->h_pinned, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            if (ctx->h_pinned[0] == 0) break;
+          }
+          if (it == max_iter) break;
+          CU(eng.inv(g, eps, b, NU, act, 0, nullptr));                     // g = eps^{-1}
+          CU(eng.gemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // al g
+          CU(eng.gemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // be g
+          CU(eng.gemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // al g be
+          CU(eng.gemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // be g al
+          lead_update_kernel<<<eg, 256, 0, s>>>(eps, epss, T[2], T[3], b, done);
+          KCHECK();
+          CU(eng.gemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -al g al
+          CU(eng.gemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -be g be
+          std::swap(al, T[4]);
+          std::swap(be, T[5]);
+        }
+        // ---- surface function and its residual
+        CU(eng.inv(g, epss, b, NU, any_warm ? cold : nullptr, 0, nullptr));
+        if ((st = residual(g, res, any_warm ? cold : nullptr)) != NEGF_OK) return st;
+        // ---- Newton polishing of the decimation result above the target
+        set_need_kernel<<<(NU + 255) / 256, 256, 0, s>>>(res, need, NU, target, cold);
+        KCHECK();
+        BMat gn = eps;   // decimation slots are free now
+        for (int step = 0; step < 3; ++step) {
+          const int cnt = n_set(need);
+          if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
+          if (cnt == 0) break;
+          if ((st = newton_step(need, gn)) != NEGF_OK) return st;
+          newton_accept_kernel<<<NU, 256, 0, s>>>(g, gn, b, res, resn, need, target, nsteps);
+          KCHECK();
+          // units that took the step continue from T1/T2 (K, F of the accepted g)
+        }
+      }
+      if (gs_L)
+        CU(cudaMemcpyAsync((zc*)gs_L + o[3] + (long long)e0 * bb, g.p, blk * U, cudaMemcpyDeviceToDevice, s));
+      if (gs_R)
+        CU(cudaMemcpyAsync((zc*)gs_R + o[3] + (long long)e0 * bb, g.p + (long long)U * bb, blk * U,
+                           cudaMemcpyDeviceToDevice, s));
       // sigma = al0 g be0 (left units -> sigma_L, right -> sigma_R)
       CU(eng.gemm(T[0], al0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU));
       zc* sL = (zc*)sigma_L + o[3] + (long long)e0 * bb;
@@ -1143,8 +1302,9 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       CU(eng.gemm(BMat{sL, bb}, T[0], OP_N, be0, OP_N, ONE, NOMAT, ZERO, b, U));
       CU(eng.gemm(BMat{sR, bb}, BMat{T[0].p + (long long)U * bb, bb}, OP_N,
                   BMat{be0.p + (long long)U * bb, bb}, OP_N, ONE, NOMAT, ZERO, b, U));
-      obc_finish_kernel<<<(U + 127) / 128, 128, 0, s>>>(done, res, it_arr, U, status ? status + o[2] + e0 : nullptr,
-                                                        iters ? iters + 2 * (o[2] + e0) : nullptr, accept);
+      obc_finish_kernel<<<(U + 127) / 128, 128, 0, s>>>(
+          done, res, it_arr, nsteps, U, status ? status + o[2] + e0 : nullptr,
+          iters ? iters + 2 * (o[2] + e0) : nullptr, newton ? newton + 2 * (o[2] + e0) : nullptr, accept);
       KCHECK();
     }
   }

@@ -31,7 +31,8 @@ MIXED_TF32 = 2
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
            "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_profile_enable",
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
-           "negf_block_gemm_noalloc"]
+           "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
+           "negf_mlp_forward", "negf_mlp_train_step"]
 KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
 
 
@@ -45,6 +46,13 @@ class _System(C.Structure):
     _fields_ = [("ndev", C.c_int32), ("nb", C.POINTER(C.c_int32)), ("bs", C.POINTER(C.c_int32)),
                 ("ne", C.POINTER(C.c_int32)), ("H_diag", C.c_void_p), ("H_up", C.c_void_p),
                 ("S_diag", C.c_void_p), ("S_up", C.c_void_p), ("energy", C.c_void_p), ("eta", C.c_double)]
+
+
+class MlpDims(C.Structure):
+    """negf_mlp_dims (include/negf_warmstart.h)."""
+    _fields_ = [("b", C.c_int32), ("hidden", C.c_int32), ("k0", C.c_int32), ("k0p", C.c_int32),
+                ("nout", C.c_int32), ("off_W1", C.c_int64), ("off_c1", C.c_int64), ("off_W2", C.c_int64),
+                ("off_c2", C.c_int64), ("off_W3", C.c_int64), ("off_c3", C.c_int64), ("n_params", C.c_int64)]
 
 
 class _Scattering(C.Structure):
@@ -70,7 +78,14 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_last_error.restype = C.c_char_p
     lib.negf_ctx_sync.argtypes = [vp, vp]
     lib.negf_layout.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64)]
-    lib.negf_obc.argtypes = [vp, C.POINTER(_System), dbl, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_obc.argtypes = [vp, C.POINTER(_System), dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_mlp_get_dims.argtypes = [i32, i32, C.POINTER(MlpDims)]
+    lib.negf_mlp_workspace_bytes.argtypes = [C.POINTER(MlpDims), i32]
+    lib.negf_mlp_workspace_bytes.restype = sz
+    lib.negf_mlp_pack.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.negf_mlp_forward.argtypes = [vp, C.POINTER(MlpDims), vp, i32, vp, vp, vp]
+    lib.negf_mlp_train_step.argtypes = [vp, C.POINTER(MlpDims), vp, vp, vp, vp, i32, C.c_float, i32, vp, i32, vp,
+                                        vp, vp, i32, vp]
     lib.negf_rgf_retarded.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, C.POINTER(_Scattering),
                                       vp, vp, vp, vp, vp]
     lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
@@ -85,7 +100,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_profile_read.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.negf_profile_reset.argtypes = [vp]
     for name in EXPORTS:
-        if name != "negf_last_error":
+        if name not in ("negf_last_error", "negf_mlp_workspace_bytes"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -265,10 +280,11 @@ def _scat_ptr(scat):
 # ---------------------------------------------------------------------------
 
 def negf_obc(ctx: Context, sys: System, sigma_L, sigma_R, iters=None, status=None, tol=1e-12, max_iter=100,
-             stream=None):
+             stream=None, g0_L=None, g0_R=None, gs_L=None, gs_R=None, newton=None):
     s = sys.c()
-    ctx.check(ctx.lib.negf_obc(ctx.h, C.byref(s), float(tol), int(max_iter), None, None, _ptr(sigma_L),
-                               _ptr(sigma_R), _ptr(iters), _ptr(status), _stream(stream)))
+    ctx.check(ctx.lib.negf_obc(ctx.h, C.byref(s), float(tol), int(max_iter), _ptr(g0_L), _ptr(g0_R),
+                               _ptr(sigma_L), _ptr(sigma_R), _ptr(gs_L), _ptr(gs_R), _ptr(iters), _ptr(newton),
+                               _ptr(status), _stream(stream)))
 
 
 def negf_rgf_retarded(ctx: Context, sys: System, prec, sigma_L, sigma_R, scat=None, GR_diag=None, GR_up=None,
@@ -360,3 +376,52 @@ def negf_block_gemm_noalloc(A, B, D, opA=0, opB=0, alpha=1.0, beta=0.0, C_=None,
                                      _stream(stream))
     if rc != NEGF_OK:
         raise NegfError(rc, lib.negf_last_error(None).decode())
+
+
+# ---------------------------------------------------------------------------
+# warm-start network (include/negf_warmstart.h)
+# ---------------------------------------------------------------------------
+
+def negf_mlp_get_dims(b: int, hidden: int = 512) -> MlpDims:
+    lib = load_library()
+    d = MlpDims()
+    rc = lib.negf_mlp_get_dims(int(b), int(hidden), C.byref(d))
+    if rc != NEGF_OK:
+        raise NegfError(rc, lib.negf_last_error(None).decode())
+    return d
+
+
+def negf_mlp_workspace_bytes(dims: MlpDims, n: int) -> int:
+    return int(load_library().negf_mlp_workspace_bytes(C.byref(dims), int(n)))
+
+
+def mlp_rows(n: int) -> int:
+    """Rows of the feature / activation buffers for n samples (multiple of 128)."""
+    return (int(n) + 127) // 128 * 128
+
+
+def negf_mlp_pack(ctx: Context, b: int, H00, H01, lead, E, X=None, stream=None):
+    """Feature rows (BF16, returned as a torch.bfloat16 [NP, K0P] tensor) of the samples
+    (lead[s], E[s]); H00/H01 are [nlead, b, b] complex128 device tensors."""
+    n = int(lead.numel())
+    d = negf_mlp_get_dims(b, 128)
+    if X is None:
+        X = torch.empty((mlp_rows(n), d.k0p), dtype=torch.bfloat16, device=lead.device)
+    ctx.check(ctx.lib.negf_mlp_pack(ctx.h, int(b), n, int(H00.shape[0]), _ptr(H00), _ptr(H01), _ptr(lead),
+                                    _ptr(E), _ptr(X), _stream(stream)))
+    return X
+
+
+def negf_mlp_forward(ctx: Context, dims: MlpDims, params, n: int, X, g0=None, stream=None):
+    if g0 is None:
+        g0 = torch.empty((int(n), dims.b, dims.b), dtype=torch.complex128, device=params.device)
+    ctx.check(ctx.lib.negf_mlp_forward(ctx.h, C.byref(dims), _ptr(params), int(n), _ptr(X), _ptr(g0),
+                                       _stream(stream)))
+    return g0
+
+
+def negf_mlp_train_step(ctx: Context, dims: MlpDims, params, adam_m, adam_v, grad, step: int, lr: float, n: int, X,
+                        g_target, loss, update: bool = True, rows=None, n_set: int = 0, stream=None):
+    ctx.check(ctx.lib.negf_mlp_train_step(ctx.h, C.byref(dims), _ptr(params), _ptr(adam_m), _ptr(adam_v),
+                                          _ptr(grad), int(step), float(lr), int(n), _ptr(rows), int(n_set), _ptr(X),
+                                          _ptr(g_target), _ptr(loss), int(bool(update)), _stream(stream)))

@@ -10,7 +10,7 @@ import pytest
 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "negf.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("negf.h", "negf_warmstart.h")]
 
 
 @pytest.fixture(scope="module")
@@ -23,7 +23,7 @@ def lib():
 
 
 def declared_functions():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(negf_[a-z_]+)\s*\(", txt)))
 
@@ -76,8 +76,35 @@ def test_layout_rejects_bad_shapes(lib):
 
 def test_null_arguments_are_rejected_without_a_gpu(lib):
     from paper_2602_03438_gb300 import negf
-    assert lib.negf_obc(None, None, 1e-12, 10, None, None, None, None, None, None, None) == negf.NEGF_ERR_ARG
+    assert lib.negf_obc(None, None, 1e-12, 10, None, None, None, None, None, None, None, None, None,
+                        None) == negf.NEGF_ERR_ARG
     assert lib.negf_rgf_lesser(None, None, 0, None, None, None, None, None, None, None, None, None,
                                None, None, None) == negf.NEGF_ERR_ARG
     assert lib.negf_layout(None, None) == negf.NEGF_ERR_ARG
     assert b"NULL" in lib.negf_last_error(None)
+
+
+def test_mlp_dims_match_the_oracle_layout(lib):
+    from paper_2602_03438_gb300 import negf
+    from oracle import mlp_oracle as M
+    for b, h in ((64, 512), (8, 128), (16, 256)):
+        d = negf.negf_mlp_get_dims(b, h)
+        k0, k0p, hid, nout = M.mlp_dims(b, h)
+        lay, total = M.param_layout(b, h)
+        assert (d.b, d.hidden, d.k0, d.k0p, d.nout) == (b, h, k0, k0p, nout)
+        assert [d.off_W1, d.off_c1, d.off_W2, d.off_c2, d.off_W3, d.off_c3] == [lay[k][0] for k in
+                                                                             ("W1", "c1", "W2", "c2", "W3", "c3")]
+        assert d.n_params == total
+        assert negf.negf_mlp_workspace_bytes(d, 1000) > negf.negf_mlp_workspace_bytes(d, 100) > 0
+    for b, h in ((12, 512), (64, 100), (0, 512)):
+        with pytest.raises(negf.NegfError) as ei:
+            negf.negf_mlp_get_dims(b, h)
+        assert ei.value.code == negf.NEGF_ERR_ARG
+
+
+def test_mlp_entry_points_reject_null_without_a_gpu(lib):
+    from paper_2602_03438_gb300 import negf
+    assert lib.negf_mlp_pack(None, 64, 1, 1, None, None, None, None, None, None) == negf.NEGF_ERR_ARG
+    assert lib.negf_mlp_forward(None, None, None, 1, None, None, None) == negf.NEGF_ERR_ARG
+    assert lib.negf_mlp_train_step(None, None, None, None, None, None, 1, 1e-3, 1, None, 0, None, None, None, 1,
+                                   None) == negf.NEGF_ERR_ARG

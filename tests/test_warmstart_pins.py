@@ -35,8 +35,11 @@ def test_pack_features_round_trip():
     H00, H01 = W.config5_lead(3, b=6)
     x = M.pack_features(H00, H01, -1.25)
     k0, k0p, _, _ = M.mlp_dims(6)
-    assert k0 == 3 * 36 + 1 and k0p % 128 == 0 and x.shape == (k0p,)
+    assert k0 == 3 * 36 + 1 + 64 and k0p % 128 == 0 and x.shape == (k0p,)
     assert np.all(x[k0:] == 0.0)
+    w = 2.0 ** (np.arange(32) / 4.0)
+    assert np.allclose(M.freqs(), w, rtol=1e-15, atol=0)
+    assert np.allclose(x[3 * 36 + 1:k0:2], np.sin(-1.25 * w)) and np.allclose(x[3 * 36 + 2:k0:2], np.cos(-1.25 * w))
     A, B, E = M.unpack_features(x, 6)
     assert np.allclose(A, H00, atol=1e-15) and np.allclose(B, H01, atol=1e-15) and abs(E + 1.25) < 1e-15
     assert np.allclose(M.unpack_output(M.pack_target(H01), 6), H01, atol=0)
@@ -60,12 +63,12 @@ def test_gradients_match_central_differences():
     loss, grad, _ = M.loss_and_grads(theta, X, T, b, h, quant=False)
     lay, _ = M.param_layout(b, h)
     rng = np.random.default_rng(1)
-    k0 = 3 * b * b + 1
+    k0 = M.mlp_dims(b, h)[0]
     checked = 0
     for name, (o, n) in lay.items():
         idx = rng.choice(n, size=min(n, 12), replace=False)
         if name == "W1":   # include live columns (k < K0) of W1
-            idx = np.array([r * (n // h) + c for r in range(h) for c in (0, k0 - 1)])
+            idx = np.array([r * (n // h) + c for r in range(h) for c in (0, 3 * b * b, k0 - 1)])
         for i in idx:
             eps = 1e-6
             tp, tm = theta.copy(), theta.copy()
@@ -83,7 +86,7 @@ def test_padding_columns_get_zero_gradient():
     theta, X, T, b, h = _tiny(seed=2)
     _, grad, _ = M.loss_and_grads(theta, X, T, b, h, quant=True)
     p = M.split_params(grad, b, h)
-    k0 = 3 * b * b + 1
+    k0 = M.mlp_dims(b, h)[0]
     assert np.all(p["W1"][:, k0:] == 0.0)
 
 
@@ -97,7 +100,8 @@ def test_forward_closed_form_constant_output():
 
 
 def test_relu_network_by_hand():
-    # b = 1 (K0 = 4), hidden 2: z1 = W1 x + c1 etc. written out for one sample
+    # b = 1, hidden 2: z1 = W1 x + c1 etc. written out for one sample (feature 3 is E/3;
+    # the Fourier features of E get zero weights)
     b, h = 1, 2
     lay, total = M.param_layout(b, h)
     theta = np.zeros(total)

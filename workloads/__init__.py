@@ -248,6 +248,41 @@ def config5_lead(k: int, b: int = 64, seed: int = SEED_BASE + 5) -> tuple:
     return H00, H01
 
 
+def config5_sets(b: int = 64, n_leads: int = 16, n_train_e: int = 256, n_held_e: int = 64,
+                 n_unseen: int = 4, seed: int = SEED_BASE + 5) -> dict:
+    """The warm-start workload: 16 leads x 256 training energies (4096 pairs, uniform
+    grid on [-3, 3]), 1024 held-out energies on the same leads (64 per lead, uniform
+    random, off the grid), and 4 unseen leads with 64 random energies each."""
+    rng = _rng(seed + 999)
+    leads = [config5_lead(k, b, seed) for k in range(n_leads + n_unseen)]
+    H00 = np.stack([h for h, _ in leads])
+    H01 = np.stack([t for _, t in leads])
+    grid = np.linspace(-3.0, 3.0, n_train_e)
+    train = (np.repeat(np.arange(n_leads), n_train_e).astype(np.int32), np.tile(grid, n_leads))
+    held = (np.repeat(np.arange(n_leads), n_held_e).astype(np.int32),
+            rng.uniform(-3.0, 3.0, size=n_leads * n_held_e))
+    unseen = (np.repeat(np.arange(n_leads, n_leads + n_unseen), n_held_e).astype(np.int32),
+              rng.uniform(-3.0, 3.0, size=n_unseen * n_held_e))
+    return dict(H00=H00, H01=H01, train=train, held=held, unseen=unseen)
+
+
+def mlp_init(b: int, hidden: int = 512, seed: int = SEED_BASE + 50) -> np.ndarray:
+    """Initial parameters of the warm-start network as one float32 vector in the
+    layout W1 [hidden][K0P], c1, W2 [hidden][hidden], c2, W3 [2b^2][hidden], c3:
+    weights uniform in +-sqrt(6 / fan_in) (He), biases zero, and the padding
+    columns of W1 (k >= 3b^2+65) zero."""
+    rng = _rng(seed)
+    k0 = 3 * b * b + 1 + 64          # lead blocks, E, 32 sine/cosine pairs of E
+    k0p = (k0 + 127) // 128 * 128
+    nout = 2 * b * b
+    W1 = np.zeros((hidden, k0p))
+    W1[:, :k0] = rng.uniform(-1, 1, size=(hidden, k0)) * np.sqrt(6.0 / k0)
+    W2 = rng.uniform(-1, 1, size=(hidden, hidden)) * np.sqrt(6.0 / hidden)
+    W3 = rng.uniform(-1, 1, size=(nout, hidden)) * np.sqrt(6.0 / hidden) * 0.1
+    parts = [W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), W3.ravel(), np.zeros(nout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def ideal_chain(nb: int, t: float, energy, eta: float = 1e-6, onsite: float = 0.0) -> Device:
     """b = 1 chain with every block equal to the lead (onsite, hop t)."""
     Hd = np.full((nb, 1, 1), onsite, dtype=np.complex128)
