@@ -304,8 +304,11 @@ def run_gpu(args):
     w = torch.from_numpy(dev.weights()).cuda()
     stream = torch.cuda.current_stream()
 
+    # the OBC products take the sliced FP64-class path with the mixed sweeps, FP64 otherwise
+    obc_prec = P.MIXED if prec == P.MIXED else P.FP64
+
     def obc():
-        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"])
+        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"], prec=obc_prec)
 
     def rgf(p=prec, s=sys_, o=out, ffL=fL, ffR=fR):
         P.negf_rgf_lesser(ctx, s, p, o["sigma_L"], o["sigma_R"], ffL, ffR, None, o["GR_diag"], o["GR_up"],

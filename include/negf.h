@@ -130,6 +130,11 @@ negf_status negf_layout(const negf_system* sys, int64_t* out);
  * Newton steps on the surface fixed-point equation; an energy whose surface
  * residual ||(a00 - a01 g a10) g - I||_F / sqrt(b) stays above 1e-10 gets
  * NEGF_ERR_NOCONV in status[e].  Sigma_L = a10 g_L a01, Sigma_R = a01 g_R a10.
+ * prec: NEGF_FP64 runs every product in FP64; NEGF_MIXED runs the products of the
+ * decimation, the residuals and the Newton steps on the digit-sliced BF16 tensor-core
+ * path (FP64-class: exact FP32 accumulation of 7-bit slices, ~2^-55 of the row/column
+ * scales) when 16 <= b <= 256, keeping every inverse in FP64; NEGF_MIXED_TF32 is
+ * treated as NEGF_FP64 (a TF32 product is far too coarse for the 1e-10 residual).
  *
  * Warm start (optional, per lead side): with g0_L and/or g0_R given, that side
  * first takes up to 8 plain Newton steps from the guess (each step's Stein
@@ -150,7 +155,7 @@ negf_status negf_layout(const negf_system* sys, int64_t* out);
  *                and polishing steps together, or NULL.
  *   status     : out, device int32 [sum ne] (NEGF_OK or a negative code), or NULL.
  * Requires nb >= 2 for every device. */
-negf_status negf_obc(negf_ctx* ctx, const negf_system* sys, double tol, int32_t max_iter,
+negf_status negf_obc(negf_ctx* ctx, const negf_system* sys, negf_precision prec, double tol, int32_t max_iter,
                      const void* g0_L, const void* g0_R, void* sigma_L, void* sigma_R,
                      void* gs_L, void* gs_R, int32_t* iters, int32_t* newton, int32_t* status,
                      negf_stream stream);

@@ -1105,9 +1105,9 @@ negf_status negf_rgf_lesser(negf_ctx* c, const negf_system* sys, negf_precision 
 }
 
 // ---------------------------------------------------------------------------
-negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t max_iter, const void* g0_L,
-                     const void* g0_R, void* sigma_L, void* sigma_R, void* gs_L, void* gs_R, int32_t* iters,
-                     int32_t* newton, int32_t* status, negf_stream stream) {
+negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, double tol, int32_t max_iter,
+                     const void* g0_L, const void* g0_R, void* sigma_L, void* sigma_R, void* gs_L, void* gs_R,
+                     int32_t* iters, int32_t* newton, int32_t* status, negf_stream stream) {
   Ctx* ctx = reinterpret_cast<Ctx*>(c);
   if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
   Layout L;
@@ -1117,6 +1117,8 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
   if (!sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "sigma_L and sigma_R outputs are required");
   if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000)
     return fail(ctx, NEGF_ERR_ARG, "need tol > 0 and 1 <= max_iter <= 1000");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
   for (int d = 0; d < sys->ndev; ++d)
     if (sys->nb[d] < 2) return fail(ctx, NEGF_ERR_ARG, "OBC needs nb >= 2 (the lead hop is H_{0,1})");
   CU(cudaSetDevice(ctx->device));
@@ -1134,8 +1136,11 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
     const long long bb = (long long)b * b;
     const size_t blk = sizeof(zc) * bb;
     const int nslots = 15;
-    const size_t per_unit = nslots * blk + 64 + zinv_scratch_bytes(b, 1, 0);
-    int chunk = (int)std::min<size_t>((ctx->ws_bytes - 4096) / (2 * per_unit), (size_t)32767);
+    // products on the sliced tensor-core path (FP64-class) when asked for and supported
+    const int sl = (prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
+    eng.mixed = sl;
+    const size_t per_unit = nslots * blk + 64 + zinv_scratch_bytes(b, 1, 0) + (sl ? ozt_scratch_bytes(b, 1) : 0);
+    int chunk = (int)std::min<size_t>((ctx->ws_bytes - 8192) / (2 * per_unit), (size_t)32767);
     if (chunk < 1) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one OBC energy");
     chunk = std::min(chunk, ne);
     for (int e0 = 0; e0 < ne; e0 += chunk) {
@@ -1161,6 +1166,9 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, double tol, int32_t ma
       int* n_active = (int*)p; p += 16;
       p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
       eng.inv_scratch = zinv_scratch_bytes(b, NU, 0) ? (void*)p : nullptr;
+      p += zinv_scratch_bytes(b, NU, 0);
+      p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+      eng.ozt_scratch = sl ? (void*)p : nullptr;
 
       LeadArgs la{dv, e0, U, a00.p, al0.p, be0.p, eps.p, epss.p, al.p, be.p};
       dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), NU);

@@ -78,7 +78,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_last_error.restype = C.c_char_p
     lib.negf_ctx_sync.argtypes = [vp, vp]
     lib.negf_layout.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64)]
-    lib.negf_obc.argtypes = [vp, C.POINTER(_System), dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_obc.argtypes = [vp, C.POINTER(_System), C.c_int, dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_mlp_get_dims.argtypes = [i32, i32, C.POINTER(MlpDims)]
     lib.negf_mlp_workspace_bytes.argtypes = [C.POINTER(MlpDims), i32]
     lib.negf_mlp_workspace_bytes.restype = sz
@@ -280,9 +280,9 @@ def _scat_ptr(scat):
 # ---------------------------------------------------------------------------
 
 def negf_obc(ctx: Context, sys: System, sigma_L, sigma_R, iters=None, status=None, tol=1e-12, max_iter=100,
-             stream=None, g0_L=None, g0_R=None, gs_L=None, gs_R=None, newton=None):
+             stream=None, g0_L=None, g0_R=None, gs_L=None, gs_R=None, newton=None, prec=FP64):
     s = sys.c()
-    ctx.check(ctx.lib.negf_obc(ctx.h, C.byref(s), float(tol), int(max_iter), _ptr(g0_L), _ptr(g0_R),
+    ctx.check(ctx.lib.negf_obc(ctx.h, C.byref(s), int(prec), float(tol), int(max_iter), _ptr(g0_L), _ptr(g0_R),
                                _ptr(sigma_L), _ptr(sigma_R), _ptr(gs_L), _ptr(gs_R), _ptr(iters), _ptr(newton),
                                _ptr(status), _stream(stream)))
 

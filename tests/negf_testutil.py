@@ -35,7 +35,7 @@ def block_err(got, ref):
     return num / max(den, 1e-300)
 
 
-def run_gpu(P, ctx, devs, prec, lesser=True, obc=True, sigma=None, scat=True, obs=True):
+def run_gpu(P, ctx, devs, prec, lesser=True, obc=True, sigma=None, scat=True, obs=True, obc_prec=None):
     """Run OBC (or use given sigma), RGF and observables on the GPU; return numpy outputs
     split per device."""
     if not isinstance(devs, (list, tuple)):
@@ -44,7 +44,8 @@ def run_gpu(P, ctx, devs, prec, lesser=True, obc=True, sigma=None, scat=True, ob
     out = P.allocate_outputs(sys_, lesser=lesser)
     sc = P.Scattering.from_devices(devs) if scat else None
     if obc:
-        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"])
+        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"],
+                   prec=P.FP64 if obc_prec is None else obc_prec)
     else:
         sl, sr = sigma
         out["sigma_L"].copy_(torch.from_numpy(np.ascontiguousarray(sl).reshape(-1)))

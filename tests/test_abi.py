@@ -76,7 +76,7 @@ def test_layout_rejects_bad_shapes(lib):
 
 def test_null_arguments_are_rejected_without_a_gpu(lib):
     from paper_2602_03438_gb300 import negf
-    assert lib.negf_obc(None, None, 1e-12, 10, None, None, None, None, None, None, None, None, None,
+    assert lib.negf_obc(None, None, 0, 1e-12, 10, None, None, None, None, None, None, None, None, None,
                         None) == negf.NEGF_ERR_ARG
     assert lib.negf_rgf_lesser(None, None, 0, None, None, None, None, None, None, None, None, None,
                                None, None, None) == negf.NEGF_ERR_ARG

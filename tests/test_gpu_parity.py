@@ -229,3 +229,19 @@ def test_argument_errors(P, ctx):
     bad.eta = -1.0
     with pytest.raises(P.NegfError):
         P.negf_rgf_retarded(ctx, bad, P.FP64, out["sigma_L"], out["sigma_R"], None, out["GR_diag"])
+
+
+# --- OBC with the FP64-class sliced products -------------------------------------------------
+
+@pytest.mark.parametrize("nb,b", [(2, 16), (3, 33), (2, 64), (2, 128), (2, 192), (2, 256)])
+def test_obc_mixed_products_match_oracle(P, ctx, nb, b):
+    dev = strong_leads(W.banded_device(nb, b, 6, seed=500 + b, overlap=True), seed=b)
+    r64 = run_gpu(P, ctx, dev, P.FP64, lesser=False, obs=False)[0]
+    rmx = run_gpu(P, ctx, dev, P.FP64, lesser=False, obs=False, obc_prec=P.MIXED)[0]
+    assert np.all(rmx["obc_status"] == 0)
+    for e in range(dev.ne):
+        ref = O.lead_self_energies(dev, dev.energy[e] + 1j * dev.eta)
+        for k, sref in (("sigma_L", ref[0]), ("sigma_R", ref[1])):
+            assert np.linalg.norm(rmx[k][e] - sref) <= TOL_FP64 * np.linalg.norm(sref), (e, k)
+        # the same stopping rule: decimation steps agree with the FP64 run's
+        assert np.abs(rmx["iters"][e] - r64["iters"][e]).max() <= 1
