@@ -19,7 +19,8 @@
 //    FP32 accumulator per d (8 accumulators in TMEM).  With K = 2n real terms the
 //    largest group sum is 8 * 64 * 64 * 2n < 2^24 for n <= 256: exact;
 //  * the epilogue forms sum_d G_d 2^(7(9-d)) as two exact int64 halves, rebuilds
-//    each double with integer operations, scaled by 2^(e_A + e_B - 63), and adds them.
+//    each double with integer operations, scaled by 2^(e_A + e_B - 63), and adds them
+//    (GB300's FP64 pipe is narrow: the recombination stays in the integer units).
 // The error is ~2^-55 of |row of A| |column of B| (truncation of the digits and of
 // the pairs with s + t > 9): FP64-class for the RGF tolerances.  (Rows and columns
 // keep their own scales; entries far below their row's or column's largest entry
@@ -645,7 +646,8 @@ __device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src
       : "memory");
 }
 
-constexpr int NT_T = 192;   // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMAs
+constexpr int NPW = 8;                 // B-digit producer / epilogue warps
+constexpr int NT_T = 32 * (NPW + 2);   // + warp NPW bulk copies, warp NPW+1 MMAs
 
 template <int CL>
 __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages im, int* err, int unit_alpha_beta) {
@@ -666,9 +668,9 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   const int nchunks = im.nchunks;
 
   if (tid == 0) {
-    // full[s]: the A copy producer (expect_tx) and the four B producer warps
-    mbar_init(&full[0], 5);
-    mbar_init(&full[1], 5);
+    // full[s]: the A copy producer (expect_tx) and the NPW B producer warps
+    mbar_init(&full[0], NPW + 1);
+    mbar_init(&full[1], NPW + 1);
     mbar_init(&empty[0], CL);
     mbar_init(&empty[1], CL);
     mbar_init(done, 1);
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   const int* eB = im.eb + (size_t)u * n;
   cluster_sync();   // every member's barriers are initialized before copies arrive
 
-  if (warp == 4) {
+  if (warp == NPW) {
     // ---------------- A: this member's 1/CL of the digit image, multicast to every member
     if (lane == 0) {
       const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks) * A_IMG;
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
                            (uint16_t)((1u << CL) - 1u));
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == NPW + 1) {
     // ---------------- MMA issue
     if (lane == 0) {
       for (int c = 0; c < nchunks; ++c) {
@@ -733,89 +735,96 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
       mma_commit(done);
     }
   } else {
-    // ---------------- warps 0-3: B digits of column bn, 4 consecutive complex k from bk,
-    // straight from complex128 into this member's stage; then the epilogue
-    const int bn = tid >> 2, bk = (tid & 3) * 4, gn = n0 + bn;
+    // ---------------- warps 0..NPW-1: B digits of column bn, 2 consecutive complex k from
+    // bk, straight from complex128 into this member's stage; then the epilogue
+    const int bn = tid >> 3, bk = (tid & 7) * 2, gn = n0 + bn;
     const zc* B = g.B.at(u);
     const int eb_n = (gn < n) ? eB[gn] : 0;
-    zc rb[4];
+    zc rb[2];
     auto loadb = [&](int c) {
       const int k0 = c * KC;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 2; ++j) {
         const int gk = k0 + bk + j;
         rb[j] = zmake(0.0, 0.0);
         if (gn < n && gk < n) rb[j] = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
       }
     };
     if (nchunks > 0) loadb(0);
+    const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
     for (int c = 0; c < nchunks; ++c) {
       const int s = c & 1;
       if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
-      zc cb[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cb[j] = rb[j];
+      zc cb[2];
+      cb[0] = rb[0];
+      cb[1] = rb[1];
       if (c + 1 < nchunks) loadb(c + 1);
-      unsigned int pr[NS][2], pi[NS][2];
+      unsigned int pr[NS], pi[NS];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 2; ++j) {
         int dr[NS], di[NS];
         digits(cb[j].x, eb_n, dr);
         digits(cb[j].y, eb_n, di);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-          if (j & 1) {
-            pr[q][j >> 1] |= bf16_of_int(dr[q]) << 16;
-            pi[q][j >> 1] |= bf16_of_int(di[q]) << 16;
+          if (j) {
+            pr[q] |= bf16_of_int(dr[q]) << 16;
+            pi[q] |= bf16_of_int(di[q]) << 16;
           } else {
-            pr[q][j >> 1] = bf16_of_int(dr[q]);
-            pi[q][j >> 1] = bf16_of_int(di[q]);
+            pr[q] = bf16_of_int(dr[q]);
+            pi[q] = bf16_of_int(di[q]);
           }
         }
       }
       unsigned char* Bsl = base + s * STAGE + A_IMG;
       // B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC+bn: [Im | Re]
-      const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         unsigned char* P = Bsl + q * B_SLICE;
-        *reinterpret_cast<uint2*>(P + o1) = make_uint2(pr[q][0], pr[q][1]);
-        *reinterpret_cast<uint2*>(P + o2) = make_uint2(pi[q][0] ^ 0x80008000u, pi[q][1] ^ 0x80008000u);
-        *reinterpret_cast<uint2*>(P + o3) = make_uint2(pi[q][0], pi[q][1]);
-        *reinterpret_cast<uint2*>(P + o4) = make_uint2(pr[q][0], pr[q][1]);
+        *reinterpret_cast<unsigned int*>(P + o1) = pr[q];
+        *reinterpret_cast<unsigned int*>(P + o2) = pi[q] ^ 0x80008000u;
+        *reinterpret_cast<unsigned int*>(P + o3) = pi[q];
+        *reinterpret_cast<unsigned int*>(P + o4) = pr[q];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_local(&full[s]);
     }
-    // ---------------- epilogue: TMEM lanes 32*warp.., all 32 complex columns
+    // ---------------- epilogue: TMEM lanes 32*(warp % 4).., complex columns cbase..cbase+15.
+    // The NG exact group sums (FP32 integers) are recombined in integers as two exact
+    // int64 halves, sum_{d<HSPLIT} G_d 2^(7(HSPLIT-1-d)) and sum_{d>=HSPLIT} G_d 2^(7(NG-1-d)),
+    // each rebuilt into a double with integer operations (the FP64 pipe is narrow) and
+    // scaled by 2^(e_A + e_B - 7(NS+1)); the two doubles are added once.
     if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + 32 * warp + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    const int quad = warp & 3, cbase = (warp >> 2) * (TNC / 2);
+    const int row = m0 + 32 * quad + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
     zc* D = g.D.at(u);
     const zc* Cm = g.C.p ? g.C.at(u) : nullptr;
     const int* eA = im.ea + (size_t)u * n;
     const int er = (row < n) ? eA[row] : 0;
 #pragma unroll 1
-    for (int cc = 0; cc < TNC / 8; ++cc) {
-      const int j0 = 8 * cc;
-      long long hre[8], him[8], lre[8], lim[8];
+    for (int cc = 0; cc < TNC / 16; ++cc) {
+      const int j0 = cbase + 8 * cc;
+      long long hre[8], lre[8], him[8], lim[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) { hre[j] = 0; him[j] = 0; lre[j] = 0; lim[j] = 0; }
+      for (int part = 0; part < 2; ++part) {
+        uint32_t v[NG][8];
 #pragma unroll
-      for (int d = 0; d < NG; ++d) {
-        uint32_t vr[8], vi[8];
-        TC_LD8(lane_base + (uint32_t)(d * NR + j0), vr);
-        TC_LD8(lane_base + (uint32_t)(d * NR + TNC + j0), vi);
+        for (int d = 0; d < NG; ++d) TC_LD8(lane_base + (uint32_t)(d * NR + part * TNC + j0), v[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int sh = (d < HSPLIT) ? 7 * (HSPLIT - 1 - d) : 7 * (NG - 1 - d);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const long long gr = ((long long)__float2int_rn(__uint_as_float(vr[j]))) << sh;
-          const long long gi = ((long long)__float2int_rn(__uint_as_float(vi[j]))) << sh;
-          if (d < HSPLIT) { hre[j] += gr; him[j] += gi; }
-          else { lre[j] += gr; lim[j] += gi; }
+          long long h = 0, l = 0;
+#pragma unroll
+          for (int d = 0; d < NG; ++d) {
+            const long long gv = (long long)__float2int_rn(__uint_as_float(v[d][j]));
+            if (d < HSPLIT) h += gv << (7 * (HSPLIT - 1 - d));
+            else l += gv << (7 * (NG - 1 - d));
+          }
+          if (part == 0) { hre[j] = h; lre[j] = l; }
+          else { him[j] = h; lim[j] = l; }
         }
       }
       if (row < n && !s_fail) {
@@ -825,8 +834,8 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
           if (gcol < n) {
             const int p = er + eB[gcol] - 7 * (NS + 1);
             const int ph = p + 7 * (NG - HSPLIT);
-            zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
-                           ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            const zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
+                                 ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
             zc v;
             if (unit_alpha_beta) {
               v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
