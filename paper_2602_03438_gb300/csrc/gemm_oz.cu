@@ -220,6 +220,19 @@ __device__ __forceinline__ unsigned int bf16_of_int(int v) {
   return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f) >> 16;
 }
 
+static_assert(NG == 8 && HSPLIT == 4, "halves() pairs the eight groups as 2 x 2 x 2");
+// group sums G_0..G_7 of one element (exact FP32 integers) -> the two int64 halves
+// h = sum_{d<4} G_d 2^(7(3-d)), l = sum_{d>=4} G_d 2^(7(7-d)), pairs first in 64-bit IMAD
+__device__ __forceinline__ void halves(const uint32_t (&v)[NG][8], int j, long long& h, long long& l) {
+  long long q[NG / 2];
+#pragma unroll
+  for (int k = 0; k < NG / 2; ++k)
+    q[k] = (long long)__float2int_rn(__uint_as_float(v[2 * k][j])) * 128 +
+           (long long)__float2int_rn(__uint_as_float(v[2 * k + 1][j]));
+  h = q[0] * (1ll << 14) + q[1];
+  l = q[2] * (1ll << 14) + q[3];
+}
+
 // exact int64 (|v| < 2^53) times 2^p as an IEEE double, built with integer operations
 __device__ __forceinline__ double ldexp_int(long long v, int p) {
   if (v == 0) return 0.0;
@@ -793,8 +806,8 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
     // ---------------- epilogue: TMEM lanes 32*(warp % 4).., complex columns cbase..cbase+15.
     // The NG exact group sums (FP32 integers) are recombined in integers as two exact
     // int64 halves, sum_{d<HSPLIT} G_d 2^(7(HSPLIT-1-d)) and sum_{d>=HSPLIT} G_d 2^(7(NG-1-d)),
-    // each rebuilt into a double with integer operations (the FP64 pipe is narrow) and
-    // scaled by 2^(e_A + e_B - 7(NS+1)); the two doubles are added once.
+    // each rebuilt into a double with integer operations and scaled by
+    // 2^(e_A + e_B - 7(NS+1)); the two doubles are added once.
     if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int quad = warp & 3, cbase = (warp >> 2) * (TNC / 2);
@@ -816,13 +829,8 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          long long h = 0, l = 0;
-#pragma unroll
-          for (int d = 0; d < NG; ++d) {
-            const long long gv = (long long)__float2int_rn(__uint_as_float(v[d][j]));
-            if (d < HSPLIT) h += gv << (7 * (HSPLIT - 1 - d));
-            else l += gv << (7 * (NG - 1 - d));
-          }
+          long long h, l;
+          halves(v, j, h, l);
           if (part == 0) { hre[j] = h; lre[j] = l; }
           else { him[j] = h; lim[j] = l; }
         }
@@ -858,6 +866,312 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   if (s_fail && tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+  cluster_sync();   // no member leaves while copies into its shared memory may be pending
+}
+
+// ===========================================================================
+// Half-width tiles, two CTAs per SM.  The same scheme on 128 x 16-complex tiles with
+// K chunks of 8 complex (32-byte rows, 32-byte swizzle): 8 accumulator groups x 32
+// columns = 256 TMEM columns and two 40 KB stages per CTA, so that two CTAs share an
+// SM and one's epilogue (integer recombination, issue-bound) overlaps the other's
+// MMAs.  The column tiles of a row tile form a cluster that shares the A digit image
+// by multicast bulk copies.
+// ===========================================================================
+constexpr int TNC2 = 16;                              // complex columns per tile
+constexpr int NR2 = 2 * TNC2;                         // real MMA columns (32)
+constexpr int KC2 = 8;                                // complex K per chunk
+constexpr uint32_t ROWB2 = 32;                        // bytes per smem row (16 bf16)
+constexpr uint32_t A_SLICE2 = TM * ROWB2;             // 4 KB
+constexpr uint32_t B_SLICE2 = NR2 * ROWB2;            // 1 KB
+constexpr uint32_t A_IMG2 = NS * A_SLICE2;            // 32 KB: one chunk of one A row tile
+constexpr uint32_t STAGE2 = A_IMG2 + NS * B_SLICE2;   // 40 KB
+constexpr uint32_t SMEM2 = 2 * STAGE2 + 1024 + 64;
+constexpr int NT2 = 192;                              // warps 0-3 B digits + epilogue, 4 copies, 5 MMAs
+
+// K-major, 32-byte swizzle: 8-row atoms of 256 B; 16-byte chunk index XOR (row>>2)&1
+__device__ __forceinline__ uint32_t sw32(int r, int c) {   // c = bf16 column in [0, 16)
+  return (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((((c >> 3) ^ ((r & 7) >> 2)) & 1) << 4) + (c & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)6 << 61;                    // 32-byte swizzle
+  return d;
+}
+
+// kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128, N = 32
+constexpr uint32_t IDESC2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR2 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC2), "r"(acc)
+      : "memory");
+}
+
+// A operand digit images for the half-width tiles: one CTA per (64 rows, unit); each
+// thread owns a row and 2 consecutive complex k of every 8-complex chunk
+__global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImages im) {
+  const int u = blockIdx.y;
+  if (g.active && !g.active[u]) return;
+  constexpr int RB = 64;
+  const int n = g.n, r0 = blockIdx.x * RB, tm = r0 / TM;
+  const zc* A = g.A.at(u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int es[RB];
+  __shared__ double part[4][RB];
+  // ---- row scales of op(A): rows of A (op N, a warp per row) or columns of A (op H)
+  if (g.opA == OP_N) {
+    for (int r = warp; r < RB; r += 8) {
+      const int gm = r0 + r;
+      double v = 0.0;
+      if (gm < n)
+        for (int k = lane; k < n; k += 32) {
+          const zc x = A[(size_t)gm * n + k];
+          v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        }
+      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+      if (lane == 0) es[r] = scale_exp(v);
+    }
+  } else {
+    const int r = tid & 63, ks = tid >> 6, gm = r0 + r;
+    double v = 0.0;
+    if (gm < n)
+      for (int k = ks; k < n; k += 4) {
+        const zc x = A[(size_t)k * n + gm];
+        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+      }
+    part[ks][r] = v;
+    __syncthreads();
+    if (tid < RB) {
+      double w = 0.0;
+      for (int q = 0; q < 4; ++q) w = fmax(w, part[q][tid]);
+      es[tid] = scale_exp(w);
+    }
+  }
+  __syncthreads();
+  if (tid < RB && r0 + tid < n) im.ea[(size_t)u * n + r0 + tid] = es[tid];
+  const int rl = tid >> 2, ak = (tid & 3) * 2, gm = r0 + rl, am = gm - tm * TM;
+  const int e = es[rl];
+  for (int c = 0; c < im.nchunks; ++c) {
+    const int k0 = c * KC2;
+    unsigned int pr[NS], pi[NS];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gk = k0 + ak + j;
+      zc v = zmake(0.0, 0.0);
+      if (gm < n && gk < n) v = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+      int dr[NS], di[NS];
+      digits(v.x, e, dr);
+      digits(v.y, e, di);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        if (j) {
+          pr[q] |= bf16_of_int(dr[q]) << 16;
+          pi[q] |= bf16_of_int(di[q]) << 16;
+        } else {
+          pr[q] = bf16_of_int(dr[q]);
+          pi[q] = bf16_of_int(di[q]);
+        }
+      }
+    }
+    unsigned char* img = im.a + ((size_t)(u * im.tiles_m + tm) * im.nchunks + c) * A_IMG2;
+    const uint32_t o_r = sw32(am, ak), o_i = sw32(am, KC2 + ak);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      *reinterpret_cast<unsigned int*>(img + q * A_SLICE2 + o_r) = pr[q];
+      *reinterpret_cast<unsigned int*>(img + q * A_SLICE2 + o_i) = pi[q];
+    }
+  }
+}
+
+template <int CL>
+__global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages im, int* err, int unit_alpha_beta) {
+  const int u = blockIdx.z;
+  if (g.active && !g.active[u]) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE2);   // full[2], empty[2], done
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE2 + 48);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = g.n;
+  const int tm = blockIdx.y, tn = blockIdx.x;
+  const int m0 = tm * TM, n0 = tn * TNC2;
+  const int nchunks = im.nchunks;
+
+  if (tid == 0) {
+    mbar_init(&full[0], 5);   // the A copy producer (expect_tx) and the four B producer warps
+    mbar_init(&full[1], 5);
+    mbar_init(&empty[0], CL);
+    mbar_init(&empty[1], CL);
+    mbar_init(done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t rank = cluster_ctarank();
+  const uint32_t lbase = smem_u32(base);
+  const int* eB = im.eb + (size_t)u * n;
+  cluster_sync();   // every member's barriers are initialized before copies arrive
+
+  if (warp == 4) {
+    // ---------------- A: this member's 1/CL of the digit image, multicast to every member
+    if (lane == 0) {
+      const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks) * A_IMG2;
+      constexpr uint32_t APART = A_IMG2 / CL;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+        const uint32_t st_off = (uint32_t)(s * STAGE2);
+        mbar_expect_tx(&full[s], A_IMG2);
+        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)c * A_IMG2 + rank * APART, APART,
+                           &full[s], (uint16_t)((1u << CL) - 1u));
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issue: 36 slice pairs (s + t <= NS + 1), one K step per chunk
+    if (lane == 0) {
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (!mbar_wait_cluster(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st_off = (uint32_t)(s * STAGE2);
+        const uint64_t da = sdesc32(lbase + st_off), db = sdesc32(lbase + st_off + A_IMG2);
+        const uint32_t acc_on = (c == 0) ? 0u : 1u;
+#pragma unroll
+        for (int gsum = 0; gsum < NS; ++gsum) {
+#pragma unroll
+          for (int ps = 0; ps <= gsum; ++ps) {
+            const int pt = gsum - ps;
+            mma_bf16_n32(tmem + (uint32_t)(gsum * NR2), da + (uint64_t)((ps * A_SLICE2) >> 4),
+                         db + (uint64_t)((pt * B_SLICE2) >> 4), ps == 0 ? acc_on : 1u);
+          }
+        }
+        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---------------- warps 0-3: B digits of column bn at complex k = bk of every chunk,
+    // pairs of k combined across neighbouring lanes; then the epilogue
+    const int bn = tid >> 3, bk = tid & 7, gn = n0 + bn;
+    const zc* B = g.B.at(u);
+    const int eb_n = (gn < n) ? eB[gn] : 0;
+    auto loadb = [&](int c) -> zc {
+      const int gk = c * KC2 + bk;
+      zc r = zmake(0.0, 0.0);
+      if (gn < n && gk < n) r = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+      return r;
+    };
+    zc rb = nchunks > 0 ? loadb(0) : zmake(0.0, 0.0);
+    const uint32_t o1 = sw32(bn, bk), o2 = sw32(bn, KC2 + bk), o3 = sw32(TNC2 + bn, bk),
+                   o4 = sw32(TNC2 + bn, KC2 + bk);
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c & 1;
+      if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+      const zc cb = rb;
+      if (c + 1 < nchunks) rb = loadb(c + 1);
+      int dr[NS], di[NS];
+      digits(cb.x, eb_n, dr);
+      digits(cb.y, eb_n, di);
+      unsigned char* Bsl = base + s * STAGE2 + A_IMG2;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const unsigned int r0v = bf16_of_int(dr[q]), i0v = bf16_of_int(di[q]);
+        const unsigned int r1v = __shfl_down_sync(0xffffffffu, r0v, 1);
+        const unsigned int i1v = __shfl_down_sync(0xffffffffu, i0v, 1);
+        if ((bk & 1) == 0) {   // this lane and the next hold k = bk, bk + 1
+          const unsigned int pr = r0v | (r1v << 16), pi = i0v | (i1v << 16);
+          unsigned char* P = Bsl + q * B_SLICE2;
+          // B'^T: row bn: [Re | -Im] of column n0+bn;  row TNC2+bn: [Im | Re]
+          *reinterpret_cast<unsigned int*>(P + o1) = pr;
+          *reinterpret_cast<unsigned int*>(P + o2) = pi ^ 0x80008000u;
+          *reinterpret_cast<unsigned int*>(P + o3) = pi;
+          *reinterpret_cast<unsigned int*>(P + o4) = pr;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&full[s]);
+    }
+    // ---------------- epilogue: TMEM lanes 32*warp.., all 16 complex columns (see the
+    // full-width kernel for the exact integer recombination)
+    if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    zc* D = g.D.at(u);
+    const zc* Cm = g.C.p ? g.C.at(u) : nullptr;
+    const int* eA = im.ea + (size_t)u * n;
+    const int er = (row < n) ? eA[row] : 0;
+#pragma unroll 1
+    for (int cc = 0; cc < TNC2 / 8; ++cc) {
+      const int j0 = 8 * cc;
+      long long hre[8], lre[8], him[8], lim[8];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        uint32_t v[NG][8];
+#pragma unroll
+        for (int d = 0; d < NG; ++d) TC_LD8(lane_base + (uint32_t)(d * NR2 + part * TNC2 + j0), v[d]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          long long h, l;
+          halves(v, j, h, l);
+          if (part == 0) { hre[j] = h; lre[j] = l; }
+          else { him[j] = h; lim[j] = l; }
+        }
+      }
+      if (row < n && !s_fail) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int gcol = n0 + j0 + j;
+          if (gcol < n) {
+            const int p = er + eB[gcol] - 7 * (NS + 1);
+            const int ph = p + 7 * (NG - HSPLIT);
+            const zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
+                                 ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            zc v;
+            if (unit_alpha_beta) {
+              v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
+              if (Cm && g.beta.x != 0.0) {
+                const zc cv = Cm[(size_t)row * n + gcol];
+                v = (g.beta.x > 0) ? zadd(v, cv) : zsub(v, cv);
+              }
+            } else {
+              v = zmul(g.alpha, acc);
+              if (Cm) v = zadd(v, zmul(g.beta, Cm[(size_t)row * n + gcol]));
+            }
+            D[(size_t)row * n + gcol] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_fail && tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
   }
   cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
@@ -910,19 +1224,81 @@ cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s)
   return cudaGetLastError();
 }
 
-// digitize-once variant: scales + A and B digit images
+// digitize-once variants: scales + A digit images (the larger of the two layouts)
 static int ozt_tiles_n(int n) { return ((n + TNC - 1) / TNC + kCluster - 1) / kCluster * kCluster; }
 
 size_t ozt_scratch_bytes(int n, int units) {
-  const size_t nch = (size_t)(n + KC - 1) / KC;
   const size_t tm = (size_t)(n + TM - 1) / TM;
   size_t b = sizeof(int) * 2 * (size_t)n * units;
   b = (b + 1023) & ~(size_t)1023;
-  b += (size_t)units * tm * nch * A_IMG;
+  const size_t full = (size_t)(n + KC - 1) / KC * A_IMG, half = (size_t)(n + KC2 - 1) / KC2 * A_IMG2;
+  b += (size_t)units * tm * (full > half ? full : half);
   return b;
 }
 
+// half-width tiles, two CTAs per SM; cluster = the column tiles sharing one A image
+static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(zgemm_ozs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(zgemm_ozs_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(zgemm_ozs_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int n = g.n;
+  const int tn = (n + TNC2 - 1) / TNC2;
+  const int CL = (tn % 8 == 0) ? 8 : (tn % 4 == 0) ? 4 : 2;
+  OzImages im;
+  im.nchunks = (n + KC2 - 1) / KC2;
+  im.tiles_m = (n + TM - 1) / TM;
+  im.tiles_n = (tn + CL - 1) / CL * CL;
+  unsigned char* p = (unsigned char*)scratch;
+  im.ea = (int*)p;
+  im.eb = im.ea + (size_t)n * g.units;
+  p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
+  im.a = p;
+  oz_digitize_a2_kernel<<<dim3(im.tiles_m * (TM / 64), g.units), 256, 0, s>>>(g, im);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
+                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
+                          ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(im.tiles_n, im.tiles_m, g.units);
+  cfg.blockDim = dim3(NT2, 1, 1);
+  cfg.dynamicSmemBytes = SMEM2;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (CL == 8) e = cudaLaunchKernelEx(&cfg, zgemm_ozs_kernel<8>, g, im, err, unit_ab);
+  else if (CL == 4) e = cudaLaunchKernelEx(&cfg, zgemm_ozs_kernel<4>, g, im, err, unit_ab);
+  else e = cudaLaunchKernelEx(&cfg, zgemm_ozs_kernel<2>, g, im, err, unit_ab);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// full-width tiles (one CTA per SM)
+static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
+
+// blocks up to 96: half-width tiles (less padding, two CTAs per SM); larger blocks:
+// full-width tiles (measured faster from n = 128 on)
 cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  if (g.units <= 0 || g.n <= 0) return cudaSuccess;
+  if (!scratch) return cudaErrorInvalidValue;
+  return g.n <= 96 ? zgemm_ozs(g, scratch, err, s) : zgemm_ozt_full(g, scratch, err, s);
+}
+
+static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
   constexpr int CL = kCluster;
