@@ -112,6 +112,11 @@ __device__ __forceinline__ typename CT<R>::T cmk(R a, R b) {
 
 constexpr int kInvThreads = 512;
 
+// Work split: thread t owns column c = t mod n and rows r0, r0 + rs, ... with
+// r0 = t div n, rs = kInvThreads div n (threads beyond rs * n only help with the
+// copies); the pivot row value of its column stays in a register during the update.
+// One warp finds the pivot; the row interchange is folded into the update (the old
+// row k is staged in shared memory); three barriers per step.
 template <typename R, bool SMEM>
 __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n, const int* active,
                                                            typename CT<R>::T* scratch, int32_t* status) {
@@ -123,94 +128,86 @@ __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n
   unsigned char* tail;
   if (SMEM) {
     W = reinterpret_cast<C*>(smem_raw);
-    tail = smem_raw + sizeof(C) * (size_t)n * n;
+    tail = smem_raw + sizeof(C) * (size_t)n * (n + 1);
   } else {
-    W = scratch + (size_t)u * n * n;
+    W = scratch + (size_t)u * n * (n + 1);
     tail = smem_raw;
   }
   C* prow = reinterpret_cast<C*>(tail);
   C* fcol = prow + n;
-  int* piv = reinterpret_cast<int*>(fcol + n);
-  __shared__ R red_v[kInvThreads / 32];
-  __shared__ int red_i[kInvThreads / 32];
+  C* krow = fcol + n;
+  int* piv = reinterpret_cast<int*>(krow + n);
   __shared__ int s_p;
   __shared__ int s_sing;
+  __shared__ C s_dinv;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const zc* Min = M.at(u);
   const int nn = n * n;
+  const int ld = n + 1;   // padded row stride: column reads hit distinct banks
   for (int i = tid; i < nn; i += kInvThreads) {
-    zc v = Min[i];
-    W[i] = cmk<R>((R)v.x, (R)v.y);
+    const int r = i / n, c = i - r * n;
+    const zc v = Min[i];
+    W[(size_t)r * ld + c] = cmk<R>((R)v.x, (R)v.y);
   }
   if (tid == 0) s_sing = 0;
+  const int rs = kInvThreads / n;           // >= 1 for n <= kInvThreads
+  const int mc = tid % n, r0 = tid / n;     // this thread's column and first row
+  const bool upd = r0 < rs;
   __syncthreads();
 
   for (int k = 0; k < n; ++k) {
-    // -- pivot: first row r >= k with the largest |W[r][k]|^2
-    R best = (R)-1;
-    int bi = n;
-    for (int r = k + tid; r < n; r += kInvThreads) {
-      C v = W[(size_t)r * n + k];
-      R a = v.x * v.x + v.y * v.y;
-      if (a > best) { best = a; bi = r; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      R ob = __shfl_down_sync(0xffffffffu, best, off);
-      int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-    __syncthreads();
+    // -- pivot (warp 0): first row r >= k with the largest |W[r][k]|^2
     if (tid < 32) {
-      best = (tid < kInvThreads / 32) ? red_v[tid] : (R)-1;
-      bi = (tid < kInvThreads / 32) ? red_i[tid] : n;
+      R best = (R)-1;
+      int bi = n;
+      for (int r = k + lane; r < n; r += 32) {
+        const C v = W[(size_t)r * ld + k];
+        const R a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bi = r; }
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        R ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        const R ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (tid == 0) {
+      if (lane == 0) {
         if (!(best > (R)0)) { s_sing = 1; bi = k; }
         s_p = bi;
         piv[k] = bi;
+        const C d = W[(size_t)bi * ld + k];
+        const R den = d.x * d.x + d.y * d.y;
+        s_dinv = (den > (R)0) ? cmk<R>(d.x / den, -d.y / den) : cmk<R>((R)0, (R)0);
       }
     }
     __syncthreads();
     const int p = s_p;
-    // -- swap rows p and k
-    if (p != k) {
-      for (int c = tid; c < n; c += kInvThreads) {
-        C t = W[(size_t)k * n + c];
-        W[(size_t)k * n + c] = W[(size_t)p * n + c];
-        W[(size_t)p * n + c] = t;
-      }
-      __syncthreads();
+    // -- scaled pivot row (from row p), elimination factors of the swapped rows, and a
+    //    copy of the old row k (which becomes row p)
+    if (tid < n) {
+      const C dinv = s_dinv;
+      const C v = (tid == k) ? cmk<R>((R)1, (R)0) : W[(size_t)p * ld + tid];
+      prow[tid] = cmk<R>(v.x * dinv.x - v.y * dinv.y, v.x * dinv.y + v.y * dinv.x);
+      fcol[tid] = (tid == k) ? cmk<R>((R)0, (R)0) : W[(size_t)(tid == p ? k : tid) * ld + k];
+      krow[tid] = W[(size_t)k * ld + tid];
     }
-    // -- scaled pivot row and elimination factors
-    C d = W[(size_t)k * n + k];
-    R den = d.x * d.x + d.y * d.y;
-    C dinv = (den > (R)0) ? cmk<R>(d.x / den, -d.y / den) : cmk<R>((R)0, (R)0);
-    for (int c = tid; c < n; c += kInvThreads) {
-      C v = (c == k) ? cmk<R>((R)1, (R)0) : W[(size_t)k * n + c];
-      prow[c] = cmk<R>(v.x * dinv.x - v.y * dinv.y, v.x * dinv.y + v.y * dinv.x);
-    }
-    for (int r = tid; r < n; r += kInvThreads) fcol[r] = (r == k) ? cmk<R>((R)0, (R)0) : W[(size_t)r * n + k];
     __syncthreads();
-    // -- rank-1 update of every row (row k becomes the scaled pivot row)
-    for (int i = tid; i < nn; i += kInvThreads) {
-      const int r = i / n, c = i - r * n;
-      if (r == k) {
-        W[i] = prow[c];
-      } else {
-        C w = (c == k) ? cmk<R>((R)0, (R)0) : W[i];
-        C f = fcol[r];
-        C pr = prow[c];
-        w.x = w.x - (f.x * pr.x - f.y * pr.y);
-        w.y = w.y - (f.x * pr.y + f.y * pr.x);
-        W[i] = w;
+    // -- rank-1 update: row k <- pivot row; row r <- (swapped) row r - f_r * pivot row,
+    //    the pivot column entering as 0 (so that it becomes -f_r / d)
+    if (upd) {
+      const C pc = prow[mc];
+      for (int r = r0; r < n; r += rs) {
+        const size_t i = (size_t)r * ld + mc;
+        if (r == k) {
+          W[i] = pc;
+        } else {
+          C w = (mc == k) ? cmk<R>((R)0, (R)0) : ((r == p) ? krow[mc] : W[i]);
+          const C f = fcol[r];
+          w.x = w.x - (f.x * pc.x - f.y * pc.y);
+          w.y = w.y - (f.x * pc.y + f.y * pc.x);
+          W[i] = w;
+        }
       }
     }
     __syncthreads();
@@ -220,35 +217,36 @@ __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n
     const int p = piv[k];
     if (p != k) {
       for (int r = tid; r < n; r += kInvThreads) {
-        C t = W[(size_t)r * n + k];
-        W[(size_t)r * n + k] = W[(size_t)r * n + p];
-        W[(size_t)r * n + p] = t;
+        C t = W[(size_t)r * ld + k];
+        W[(size_t)r * ld + k] = W[(size_t)r * ld + p];
+        W[(size_t)r * ld + p] = t;
       }
     }
     __syncthreads();
   }
   zc* Xo = X.at(u);
   for (int i = tid; i < nn; i += kInvThreads) {
-    C v = W[i];
+    const int r = i / n, c = i - r * n;
+    const C v = W[(size_t)r * ld + c];
     Xo[i] = zmake((double)v.x, (double)v.y);
   }
   if (tid == 0 && s_sing && status) status[u] = NEGF_ERR_SINGULAR;
 }
 
-static size_t inv_tail_bytes(int n, size_t csz) { return 2 * csz * n + sizeof(int) * n + 16; }
+static size_t inv_tail_bytes(int n, size_t csz) { return 3 * csz * n + sizeof(int) * n + 16; }
 static const size_t kInvSmemMax = 200 * 1024;
 
 size_t zinv_scratch_bytes(int n, int units, int single) {
   const size_t csz = single ? sizeof(float2) : sizeof(double2);
-  if (csz * (size_t)n * n + inv_tail_bytes(n, csz) <= kInvSmemMax) return 0;
-  return csz * (size_t)n * n * units;
+  if (csz * (size_t)n * (n + 1) + inv_tail_bytes(n, csz) <= kInvSmemMax) return 0;
+  return csz * (size_t)n * (n + 1) * units;
 }
 
 template <typename R>
 static cudaError_t launch_inv(BMat X, BMat M, int n, int units, const int* active, void* scratch,
                               int32_t* status, cudaStream_t s) {
   typedef typename CT<R>::T C;
-  const size_t full = sizeof(C) * (size_t)n * n + inv_tail_bytes(n, sizeof(C));
+  const size_t full = sizeof(C) * (size_t)n * (n + 1) + inv_tail_bytes(n, sizeof(C));
   if (full <= kInvSmemMax) {
     cudaError_t e = cudaFuncSetAttribute(zinv_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)full);
