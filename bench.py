@@ -478,6 +478,41 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_probe(args):
+    """One building block of the sweeps alone, for kernel profiling: --probe gemm runs the
+    batched block product D = A B and --probe inverse the block inverse, on `ne` random
+    complex128 b x b blocks (config-2 shape by default), `warmup` + `steps` calls, in the
+    precision of --prec.  Prints the device time per call; not a bench line."""
+    import torch
+    import paper_2602_03438_gb300 as P
+    torch.cuda.set_device(0)
+    prec = {"mixed": P.MIXED, "fp64": P.FP64, "mixed_tf32": P.MIXED_TF32}[args.prec]
+    gen = torch.Generator(device="cuda").manual_seed(20260002)
+    shape = (args.ne, args.b, args.b)
+    A = torch.randn(shape, dtype=torch.complex128, device="cuda", generator=gen)
+    B = torch.randn(shape, dtype=torch.complex128, device="cuda", generator=gen)
+    if args.probe == "inverse":   # diagonally dominant: well conditioned blocks
+        A = A + args.b * torch.eye(args.b, dtype=torch.complex128, device="cuda")
+    D = torch.empty_like(A)
+    ctx = P.Context(0, int(args.workspace_gb * (1 << 30)))
+    call = (lambda: P.negf.negf_block_gemm(ctx, prec, A, B, D)) if args.probe == "gemm" else \
+        (lambda: P.negf.negf_block_inverse(ctx, prec, A, D))
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the probe")
+    print(json.dumps({"probe": args.probe, "b": args.b, "units": args.ne, "precision": args.prec,
+                      "ms_per_call": e0.elapsed_time(e1) / args.steps}))
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,8 +529,11 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", choices=["gemm", "inverse"], default=None)
     args = ap.parse_args(argv)
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -300,9 +300,10 @@ struct Engine {
     return e;
   }
   cudaError_t inv(BMat X, BMat M, int n, int units, const int* active, int single, int32_t* status) {
-    begin(single ? K_INV_F32 : K_INV_F64);
+    const bool masked = active != nullptr;   // masked launches do an unknown share of the work
+    begin(masked ? K_OTHER : (single ? K_INV_F32 : K_INV_F64));
     cudaError_t e = zinv(X, M, n, units, active, single, inv_scratch, status, s);
-    end(8.0 * (double)n * n * n * units, 32.0 * (double)n * n * units);
+    end(masked ? 0.0 : 8.0 * (double)n * n * n * units, masked ? 0.0 : 32.0 * (double)n * n * units);
     return e;
   }
   // X = M^{-1}.  Mixed precision: FP32 Gauss-Jordan, then `refine` steps of
