@@ -164,6 +164,46 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// instruction descriptor of kind::f16 (BF16 A/B, FP32 D, both K-major), M = 128, N columns
+__device__ __forceinline__ uint32_t idesc_n(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_d(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// One K step of the NS(NS+1)/2 slice products as a few wide MMAs.  The NS B digit
+// planes lie one after another in shared memory (NRW rows each), so planes t0 ..
+// t0+k-1 form one operand of N = k NRW rows; against A digit plane s its product
+// lands in TMEM columns (s + t) NRW, i.e. in the accumulators of the scale groups
+// s + t0 .. s + t0 + k - 1.  N <= 256 per instruction: 12 MMAs for NRW = 64, 8 for
+// NRW = 32, instead of one N = NRW MMA per pair (whose A operand would be re-read
+// from shared memory for every pair).  `first`: the s = 0 MMAs cover every group and
+// come first, so they initialize the accumulators.
+template <int NRW>
+__device__ __forceinline__ void slice_mmas(uint32_t tmem, uint64_t da, uint64_t db, uint32_t a_slice16,
+                                           uint32_t b_slice16, bool first) {
+  constexpr int KMAX = 256 / NRW;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int t0 = 0; t0 < NS - s; t0 += KMAX) {
+      const int k = (NS - s - t0) < KMAX ? (NS - s - t0) : KMAX;
+      mma_bf16_d(tmem + (uint32_t)((s + t0) * NRW), da + (uint64_t)s * a_slice16, db + (uint64_t)t0 * b_slice16,
+                 idesc_n(k * NRW), (first && s == 0) ? 0u : 1u);
+    }
+  }
+}
+
+#define TC_LD4(taddr, r)                                                                          \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"                         \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                                    \
+               : "r"(taddr))
+
 #define TC_LD8(taddr, r)                                                                          \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"          \
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
@@ -728,21 +768,10 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st_off = (uint32_t)(s * STAGE);
         const uint64_t da = sdesc64(lbase + st_off), db = sdesc64(lbase + st_off + A_IMG);
-        const uint32_t first_chunk = (c == 0) ? 1u : 0u;
 #pragma unroll
-        for (int gsum = 0; gsum < NS; ++gsum) {
-#pragma unroll
-          for (int ps = 0; ps <= gsum; ++ps) {
-            const int pt = gsum - ps;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint32_t acc = (ps == 0 && ks == 0) ? (first_chunk ^ 1u) : 1u;
-              mma_bf16(tmem + (uint32_t)(gsum * NR),
-                       da + (uint64_t)((ps * A_SLICE + ks * 32) >> 4),
-                       db + (uint64_t)((pt * B_SLICE + ks * 32) >> 4), acc);
-            }
-          }
-        }
+        for (int ks = 0; ks < 2; ++ks)   // two 16-element K steps per 64-byte row
+          slice_mmas<NR>(tmem, da + (uint64_t)((ks * 32) >> 4), db + (uint64_t)((ks * 32) >> 4), A_SLICE >> 4,
+                         B_SLICE >> 4, c == 0 && ks == 0);
         mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
       }
       mma_commit(done);
@@ -1056,16 +1085,7 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st_off = (uint32_t)(s * STAGE2);
         const uint64_t da = sdesc32(lbase + st_off), db = sdesc32(lbase + st_off + A_IMG2);
-        const uint32_t acc_on = (c == 0) ? 0u : 1u;
-#pragma unroll
-        for (int gsum = 0; gsum < NS; ++gsum) {
-#pragma unroll
-          for (int ps = 0; ps <= gsum; ++ps) {
-            const int pt = gsum - ps;
-            mma_bf16_n32(tmem + (uint32_t)(gsum * NR2), da + (uint64_t)((ps * A_SLICE2) >> 4),
-                         db + (uint64_t)((pt * B_SLICE2) >> 4), ps == 0 ? acc_on : 1u);
-          }
-        }
+        slice_mmas<NR2>(tmem, da, db, A_SLICE2 >> 4, B_SLICE2 >> 4, c == 0);
         mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
       }
       mma_commit(done);
@@ -1172,6 +1192,251 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
   if (s_fail && tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+  cluster_sync();   // no member leaves while copies into its shared memory may be pending
+}
+
+// ===========================================================================
+// Persistent variant for 96 < n <= 128: the epilogue of tile t overlaps the MMAs of
+// tile t+1.  One CTA per SM, clusters of 4 (the column tiles of one unit) walk the
+// units in turn.  Full-width tiles (128 x 32 complex, N = 64 per MMA, 512 TMEM
+// columns), K chunks of 8 complex (32-byte rows, 32-byte swizzle, two 48 KB stages;
+// the A digit images are those of the half-width kernel).  After a tile's MMAs the
+// epilogue warps drain TMEM into a shared-memory buffer of exact int32 group pairs
+// G_2k 2^7 + G_2k+1 (each group sum stays below 2^23 for n <= 128, so a pair stays
+// below 2^31), free TMEM for the next tile, and then recombine the pairs and store D
+// while the next tile's MMAs run.
+// Warps 0-7: epilogue (TMEM lanes 32*(w%4), 16 columns each); 8-15: B digits;
+// 16: A copies; 17: MMA issue.
+// ===========================================================================
+constexpr int KCP = 8;                                  // complex K per chunk
+constexpr uint32_t B_SLICE_P = NR * ROWB2;              // 2 KB: 64 B'^T rows of 32 bytes
+constexpr uint32_t STAGE_P = A_IMG2 + NS * B_SLICE_P;   // 48 KB
+constexpr uint32_t PAIR_BYTES = TM * TNC * 2 * 16;      // 128 KB: 4 int32 per element and part
+constexpr uint32_t SMEM_P = 2 * STAGE_P + PAIR_BYTES + 1024 + 128;
+constexpr int NT_P = 18 * 32;
+constexpr int CL_P = 4;
+
+template <int CL>
+__global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages im, int* err, int unit_alpha_beta) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  int4* pairs = reinterpret_cast<int4*>(base + 2 * STAGE_P);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE_P + PAIR_BYTES);
+  uint64_t* full = bars;           // [2]
+  uint64_t* empty = bars + 2;      // [2]
+  uint64_t* done = bars + 4;       // MMAs of a tile complete
+  uint64_t* tfree = bars + 5;      // TMEM drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = g.n;
+  const int nchunks = (n + KCP - 1) / KCP;
+  const uint32_t rank = cluster_ctarank();
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  const int n0 = (int)rank * TNC;
+
+  if (tid == 0) {
+    mbar_init(&full[0], 9);   // the A copy (expect_tx) and the eight B warps
+    mbar_init(&full[1], 9);
+    mbar_init(&empty[0], CL);
+    mbar_init(&empty[1], CL);
+    mbar_init(done, 1);
+    mbar_init(tfree, 8);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lbase = smem_u32(base);
+  cluster_sync();   // every member's barriers are initialized before copies arrive
+  auto skip = [&](int u) { return g.active && !g.active[u]; };
+
+  if (warp == 16) {
+    // ---------------- A: this member's quarter of each chunk's digit image, multicast
+    if (lane == 0) {
+      constexpr uint32_t APART = A_IMG2 / CL;
+      uint32_t cg = 0;
+      for (int u = cid; u < g.units && !s_fail; u += ncl) {
+        if (skip(u)) continue;
+        const unsigned char* aimg = im.a + (size_t)u * im.tiles_m * nchunks * A_IMG2;
+        for (int c = 0; c < nchunks; ++c, ++cg) {
+          const int st = cg & 1;
+          if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
+          mbar_expect_tx(&full[st], A_IMG2);
+          bulk_g2s_multicast(lbase + st * STAGE_P + rank * APART, aimg + (size_t)c * A_IMG2 + rank * APART, APART,
+                             &full[st], (uint16_t)((1u << CL) - 1u));
+        }
+      }
+    }
+  } else if (warp == 17) {
+    // ---------------- MMA issue
+    if (lane == 0) {
+      uint32_t cg = 0, tiles = 0;
+      for (int u = cid; u < g.units && !s_fail; u += ncl) {
+        if (skip(u)) continue;
+        if (tiles > 0 && !mbar_wait(tfree, (tiles - 1) & 1)) { s_fail = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < nchunks; ++c, ++cg) {
+          const int st = cg & 1;
+          if (!mbar_wait_cluster(&full[st], (cg >> 1) & 1)) { s_fail = 1; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = sdesc32(lbase + st * STAGE_P), db = sdesc32(lbase + st * STAGE_P + A_IMG2);
+          slice_mmas<NR>(tmem, da, db, A_SLICE2 >> 4, B_SLICE_P >> 4, c == 0);
+          mma_commit_multicast(&empty[st], (uint16_t)((1u << CL) - 1u));
+        }
+        if (s_fail) break;
+        mma_commit(done);
+        ++tiles;
+      }
+    }
+  } else if (warp >= 8) {
+    // ---------------- B digits: column bn, complex k = bk of every chunk (neighbouring lanes
+    // hold k and k+1 and are joined by a shuffle); the next chunk's value (of this unit
+    // or the next) is loaded while this one is digitized
+    const int tb = tid - 256, bn = tb >> 3, bk = tb & 7, gn = n0 + bn;
+    const uint32_t o1 = sw32(bn, bk), o2 = sw32(bn, KCP + bk), o3 = sw32(TNC + bn, bk), o4 = sw32(TNC + bn, KCP + bk);
+    auto next_unit = [&](int u) {
+      for (u += ncl; u < g.units && skip(u); u += ncl) {
+      }
+      return u;
+    };
+    auto load1 = [&](int u, int c) -> zc {
+      const zc* B = g.B.at(u);
+      const int gk = c * KCP + bk;
+      zc r = zmake(0.0, 0.0);
+      if (gn < n && gk < n) r = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
+      return r;
+    };
+    int u = cid;
+    if (u < g.units && skip(u)) u = next_unit(u);
+    int c = 0;
+    zc rb = zmake(0.0, 0.0);
+    if (u < g.units) rb = load1(u, 0);
+    uint32_t cg = 0;
+    while (u < g.units && !s_fail) {
+      const int eb_n = (gn < n) ? im.eb[(size_t)u * n + gn] : 0;
+      const zc cur = rb;
+      int u2 = u, c2 = c + 1;
+      if (c2 == nchunks) { c2 = 0; u2 = next_unit(u); }
+      if (u2 < g.units) rb = load1(u2, c2);
+      const int st = cg & 1;
+      if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
+      int dr[NS], di[NS];
+      digits(cur.x, eb_n, dr);
+      digits(cur.y, eb_n, di);
+      unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const unsigned int r0v = bf16_of_int(dr[q]), i0v = bf16_of_int(di[q]);
+        const unsigned int r1v = __shfl_down_sync(0xffffffffu, r0v, 1);
+        const unsigned int i1v = __shfl_down_sync(0xffffffffu, i0v, 1);
+        if ((bk & 1) == 0) {   // B'^T: row bn: [Re | -Im];  row TNC+bn: [Im | Re]
+          const unsigned int pr = r0v | (r1v << 16), pi = i0v | (i1v << 16);
+          unsigned char* P = Bsl + q * B_SLICE_P;
+          *reinterpret_cast<unsigned int*>(P + o1) = pr;
+          *reinterpret_cast<unsigned int*>(P + o2) = pi ^ 0x80008000u;
+          *reinterpret_cast<unsigned int*>(P + o3) = pi;
+          *reinterpret_cast<unsigned int*>(P + o4) = pr;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(&full[st]);
+      ++cg;
+      u = u2;
+      c = c2;
+    }
+  } else {
+    // ---------------- epilogue warps 0-7
+    const int quad = warp & 3, cbase = (warp >> 2) * (TNC / 2);
+    const int rl = 32 * quad + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
+    uint32_t tiles = 0;
+    for (int u = cid; u < g.units && !s_fail; u += ncl) {
+      if (skip(u)) continue;
+      if (!mbar_wait(done, tiles & 1)) { s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // phase 1: TMEM -> exact int32 group pairs in shared memory (this lane's row)
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          uint32_t v[NG][4];
+#pragma unroll
+          for (int d = 0; d < NG; ++d) TC_LD4(lane_base + (uint32_t)(d * NR + part * TNC + cbase + 4 * cc), v[d]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            int q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              q[k] = __float2int_rn(__uint_as_float(v[2 * k][j])) * 128 + __float2int_rn(__uint_as_float(v[2 * k + 1][j]));
+            pairs[(part * TNC + cbase + 4 * cc + j) * TM + rl] = make_int4(q[0], q[1], q[2], q[3]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(tfree);
+      ++tiles;
+      // phase 2: recombine and store, overlapping the next tile's MMAs; per half of this
+      // warp's 16 columns the column scales and C entries are loaded first (independent
+      // loads in flight together), then the 8 elements are rebuilt
+      const int row = rl;   // one row tile (n <= 128)
+      if (row < n) {
+        zc* D = g.D.at(u);
+        const zc* Cm = (g.C.p && !(unit_alpha_beta && g.beta.x == 0.0)) ? g.C.at(u) : nullptr;
+        const int er = im.ea[(size_t)u * n + row] - 7 * (NS + 1);
+        const int* eB = im.eb + (size_t)u * n;
+#pragma unroll 1
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int c0 = cbase + 8 * h2;
+          int ebv[8];
+          zc cv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int gcol = n0 + c0 + j;
+            ebv[j] = (gcol < n) ? eB[gcol] : 0;
+            cv[j] = (Cm && gcol < n) ? Cm[(size_t)row * n + gcol] : zmake(0.0, 0.0);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = c0 + j, gcol = n0 + col;
+            if (gcol >= n) continue;
+            const int4 qr = pairs[col * TM + rl], qi = pairs[(TNC + col) * TM + rl];
+            const long long hr = (long long)qr.x * (1ll << 14) + qr.y, lr = (long long)qr.z * (1ll << 14) + qr.w;
+            const long long hi = (long long)qi.x * (1ll << 14) + qi.y, li = (long long)qi.z * (1ll << 14) + qi.w;
+            const int p = er + ebv[j];
+            const int ph = p + 7 * (NG - HSPLIT);
+            const zc acc = zmake(ldexp_int(hr, ph) + ldexp_int(lr, p), ldexp_int(hi, ph) + ldexp_int(li, p));
+            zc v;
+            if (unit_alpha_beta) {
+              v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
+              if (Cm) v = (g.beta.x > 0) ? zadd(v, cv[j]) : zsub(v, cv[j]);
+            } else {
+              v = zmul(g.alpha, acc);
+              if (Cm) v = zadd(v, zmul(g.beta, cv[j]));
+            }
+            D[(size_t)row * n + gcol] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_fail && tid == 0) raise_error(err, NEGF_ERR_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
   cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
@@ -1287,15 +1552,68 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   return cudaGetLastError();
 }
 
+// persistent full-width tiles with the epilogue overlapping the next tile (96 < n <= 128)
+static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  static int max_clusters = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL_P;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NT_P, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_P;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (max_clusters == 0) {
+    cudaError_t e = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_P);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(CL_P, 1, 1);
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, zgemm_ozp_kernel<CL_P>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (ncl < 1) return cudaErrorInvalidConfiguration;
+    max_clusters = ncl;
+  }
+  const int n = g.n;
+  OzImages im;
+  im.nchunks = (n + KC2 - 1) / KC2;
+  im.tiles_m = 1;
+  im.tiles_n = CL_P;
+  unsigned char* p = (unsigned char*)scratch;
+  im.ea = (int*)p;
+  im.eb = im.ea + (size_t)n * g.units;
+  p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
+  im.a = p;
+  oz_digitize_a2_kernel<<<dim3(TM / 64, g.units), 256, 0, s>>>(g, im);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
+                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
+                          ? 1 : 0;
+  const int ncl = g.units < max_clusters ? g.units : max_clusters;
+  cfg.gridDim = dim3(ncl * CL_P, 1, 1);
+  e = cudaLaunchKernelEx(&cfg, zgemm_ozp_kernel<CL_P>, g, im, err, unit_ab);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // full-width tiles (one CTA per SM)
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 
-// blocks up to 96: half-width tiles (less padding, two CTAs per SM); larger blocks:
-// full-width tiles (measured faster from n = 128 on)
+// blocks up to 96: half-width tiles (less padding, two CTAs per SM); 96 < n <= 128:
+// persistent full-width tiles with the epilogue overlapping the next tile's MMAs;
+// larger blocks: full-width tiles, one CTA per tile
 cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
-  return g.n <= 96 ? zgemm_ozs(g, scratch, err, s) : zgemm_ozt_full(g, scratch, err, s);
+  if (g.n <= 96) return zgemm_ozs(g, scratch, err, s);
+  if (g.n <= 128) return zgemm_ozp(g, scratch, err, s);
+  return zgemm_ozt_full(g, scratch, err, s);
 }
 
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {

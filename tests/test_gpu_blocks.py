@@ -37,7 +37,7 @@ def _op(x, op):
 GEMM_TOL = {"FP64": 1e-13, "MIXED": 1e-13, "MIXED_TF32": 2e-6}
 
 
-@pytest.mark.parametrize("n", [1, 8, 16, 33, 64, 128, 130, 192, 256, 300])
+@pytest.mark.parametrize("n", [1, 8, 16, 33, 64, 100, 128, 130, 192, 256, 300])
 @pytest.mark.parametrize("opA,opB", [(0, 0), (2, 0), (0, 2), (2, 2)])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED", "MIXED_TF32"])
 def test_block_gemm(P, ctx, n, opA, opB, prec):
@@ -56,6 +56,25 @@ def test_block_gemm(P, ctx, n, opA, opB, prec):
     err = np.abs(got - ref).max() / max(scale, 1e-300)
     tol = 1e-13 if n < 16 else GEMM_TOL[prec]
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("n,opA,opB", [(100, 0, 0), (128, 2, 2), (128, 0, 2), (120, 2, 0)])
+def test_sliced_gemm_many_units(P, ctx, n, opA, opB):
+    """More units than resident clusters: every cluster of the persistent kernel walks
+    several units, its epilogue overlapping the next unit's products."""
+    rng = np.random.default_rng(400 + n + opA + opB)
+    U = 160
+    A, B, Cm = _rand(rng, (U, n, n)), _rand(rng, (U, n, n)), _rand(rng, (U, n, n))
+    alpha, beta = -1.0, 1.0
+    ref = alpha * (_op(A, opA) @ _op(B, opB)) + beta * Cm
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    D = torch.empty((U, n, n), dtype=torch.complex128, device="cuda")
+    P.negf.negf_block_gemm(ctx, P.MIXED, t(A), t(B), D, opA, opB, alpha, beta, t(Cm))
+    assert ctx.sync() == 0
+    got = D.cpu().numpy()
+    for u in range(U):
+        scale = np.linalg.norm(A[u]) * np.linalg.norm(B[u]) / n
+        assert np.abs(got[u] - ref[u]).max() <= 1e-13 * scale, u
 
 
 def test_sliced_gemm_wide_dynamic_range(P, ctx):

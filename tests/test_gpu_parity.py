@@ -68,9 +68,13 @@ def test_config1_fp64_full(P, ctx):
         # is O(eta), so G^< there amplifies last-bit differences of Sigma by ~1/eta
         ref = O.solve_energy(dev, e, sigma=(r["sigma_L"][e], r["sigma_R"][e]))
         _check_energy(r, e, ref, TOL_FP64)
+        # T and DOS: |delta| / max(|ref|, 1e-3 max_E |ref|) (the tolerance reading for
+        # the scalar observables; near-resonant energies at eta = 1e-6 amplify last-bit
+        # differences of G by ~1/eta in a small DOS)
         tscale = max(1e-3 * np.abs(gold[:, 1]).max(), abs(gold[e, 1]))
+        dscale = max(1e-3 * np.abs(gold[:, 3]).max(), abs(gold[e, 3]))
         assert abs(r["T"][e] - gold[e, 1]) <= 1e-8 * tscale
-        assert abs(r["dos"][e] - gold[e, 3]) <= 1e-9 * abs(gold[e, 3])
+        assert abs(r["dos"][e] - gold[e, 3]) <= 1e-9 * dscale
 
 
 def test_config1_mixed_full(P, ctx):
