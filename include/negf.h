@@ -66,7 +66,7 @@ typedef enum {
   NEGF_FP64 = 0,       /* every product, inverse and reduction in FP64                      */
   NEGF_MIXED = 1,      /* block products on the BF16 tensor cores with exact FP32
                           accumulation of 7-bit digit slices (FP64-class, ~2^-55 of the
-                          row/column scales, 16 <= b <= 256; FP64 FMA otherwise); block inverses in FP32 + two refinement steps
+                          row/column scales, 16 <= b <= 512, K in exact passes of 256; FP64 FMA otherwise); block inverses in FP32 + two refinement steps
                           whose residual uses the same product; I/O stays complex128        */
   NEGF_MIXED_TF32 = 2  /* block products as 3-term TF32 splits (hi*hi + hi*lo + lo*hi) on
                           the tensor cores, FP32 accumulate in TMEM (~1e-6 relative per
@@ -133,7 +133,7 @@ negf_status negf_layout(const negf_system* sys, int64_t* out);
  * prec: NEGF_FP64 runs every product in FP64; NEGF_MIXED runs the products of the
  * decimation, the residuals and the Newton steps on the digit-sliced BF16 tensor-core
  * path (FP64-class: exact FP32 accumulation of 7-bit slices, ~2^-55 of the row/column
- * scales) when 16 <= b <= 256, keeping every inverse in FP64; NEGF_MIXED_TF32 is
+ * scales) when 16 <= b <= 512, keeping every inverse in FP64; NEGF_MIXED_TF32 is
  * treated as NEGF_FP64 (a TF32 product is far too coarse for the 1e-10 residual).
  *
  * Warm start (optional, per lead side): with g0_L and/or g0_R given, that side
@@ -205,7 +205,7 @@ negf_status negf_observables(negf_ctx* ctx, const negf_system* sys,
  * by all units).  op: 0 = as stored, 2 = conjugate transpose.  alpha, beta: host
  * double[2] (re, im).  C may be NULL (beta ignored) or equal to D; D must not
  * overlap A or B.  NEGF_FP64: FP64 FMA; NEGF_MIXED: digit-sliced BF16 tensor-core
- * product for 16 <= n <= 256; NEGF_MIXED_TF32: 3-term TF32 split for n >= 16
+ * product for 16 <= n <= 512 (K in exact passes of 256); NEGF_MIXED_TF32: 3-term TF32 split for n >= 16
  * (FP64 FMA outside those ranges). */
 negf_status negf_block_gemm(negf_ctx* ctx, negf_precision prec, int32_t n, int32_t units, int32_t opA,
                             int32_t opB, const double* alpha, const void* A, int64_t a_stride, const void* B,

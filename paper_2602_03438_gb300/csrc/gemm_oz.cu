@@ -598,6 +598,7 @@ struct OzImages {
   int* ea;            // [unit][n] row scales of op(A)
   int* eb;            // [unit][n] column scales of op(B)
   int tiles_m, tiles_n, nchunks;
+  int c_begin, c_count;   // K chunks of this pass (the full-width kernel runs K in passes)
 };
 
 // A operand: one CTA per (32 rows, unit); each writes its rows of the 128-row tile images
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   const int n = g.n;
   const int tm = blockIdx.y, tn = blockIdx.x;
   const int m0 = tm * TM, n0 = tn * TNC;
-  const int nchunks = im.nchunks;
+  const int nchunks = im.c_count;   // chunks c_begin .. c_begin + c_count - 1 of K
 
   if (tid == 0) {
     // full[s]: the A copy producer (expect_tx) and the NPW B producer warps
@@ -748,15 +749,15 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   if (warp == NPW) {
     // ---------------- A: this member's 1/CL of the digit image, multicast to every member
     if (lane == 0) {
-      const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks) * A_IMG;
+      const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * im.nchunks) * A_IMG;
       constexpr uint32_t APART = A_IMG / CL;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
         if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
         const uint32_t st_off = (uint32_t)(s * STAGE);
         mbar_expect_tx(&full[s], A_IMG);
-        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)c * A_IMG + rank * APART, APART, &full[s],
-                           (uint16_t)((1u << CL) - 1u));
+        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)(im.c_begin + c) * A_IMG + rank * APART,
+                           APART, &full[s], (uint16_t)((1u << CL) - 1u));
       }
     }
   } else if (warp == NPW + 1) {
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
     const int eb_n = (gn < n) ? eB[gn] : 0;
     zc rb[2];
     auto loadb = [&](int c) {
-      const int k0 = c * KC;
+      const int k0 = (im.c_begin + c) * KC;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int gk = k0 + bk + j;
@@ -1443,8 +1444,10 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
 
 }  // namespace
 
-// exact group sums need NS * 64 * 64 * 2n < 2^24
-bool oz_supported(int n) { return n >= 16 && n <= 256; }
+// exact group sums need NS * 64 * 64 * 2K <= 2^24 per accumulation: the in-kernel-digit
+// kernel accumulates the whole K (n <= 256); the digitize-once kernels run K in passes
+bool oz_supported(int n) { return n >= 16 && n <= 512; }
+bool oz_inkernel_supported(int n) { return n >= 16 && n <= 256; }
 
 size_t oz_scratch_bytes(int n, int units) { return sizeof(int) * 2 * (size_t)n * units; }
 
@@ -1520,6 +1523,8 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.nchunks = (n + KC2 - 1) / KC2;
   im.tiles_m = (n + TM - 1) / TM;
   im.tiles_n = (tn + CL - 1) / CL * CL;
+  im.c_begin = 0;
+  im.c_count = im.nchunks;
   unsigned char* p = (unsigned char*)scratch;
   im.ea = (int*)p;
   im.eb = im.ea + (size_t)n * g.units;
@@ -1582,6 +1587,8 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.nchunks = (n + KC2 - 1) / KC2;
   im.tiles_m = 1;
   im.tiles_n = CL_P;
+  im.c_begin = 0;
+  im.c_count = im.nchunks;
   unsigned char* p = (unsigned char*)scratch;
   im.ea = (int*)p;
   im.eb = im.ea + (size_t)n * g.units;
@@ -1642,9 +1649,6 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
   if (e != cudaSuccess) return e;
   oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
-                       (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
-                          ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(im.tiles_n, im.tiles_m, g.units);
   cfg.blockDim = dim3(NT_T, 1, 1);
@@ -1657,9 +1661,26 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, zgemm_ozt_kernel<CL>, g, im, err, unit_ab);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  // K in passes of at most KPASS complex terms, so that every FP32 group sum stays exact
+  // (8 64 64 2 KPASS <= 2^24); later passes add alpha A_k B_k onto D (C = D, beta = 1)
+  constexpr int KPASS = 256;
+  const int per_pass = KPASS / KC;
+  for (int c0 = 0; c0 < im.nchunks; c0 += per_pass) {
+    GemmArgs gp = g;
+    if (c0 > 0) {
+      gp.C = g.D;
+      gp.beta = zmake(1.0, 0.0);
+    }
+    im.c_begin = c0;
+    im.c_count = (im.nchunks - c0) < per_pass ? (im.nchunks - c0) : per_pass;
+    const int unit_ab = ((gp.alpha.y == 0.0 && (gp.alpha.x == 1.0 || gp.alpha.x == -1.0)) &&
+                         (!gp.C.p || (gp.beta.y == 0.0 && (gp.beta.x == 0.0 || gp.beta.x == 1.0 || gp.beta.x == -1.0))))
+                            ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, zgemm_ozt_kernel<CL>, gp, im, err, unit_ab);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace negf

@@ -255,6 +255,9 @@ struct Engine {
   void* inv_scratch;   // for inverses too large for shared memory
   void* oz_scratch = nullptr;   // per-row/column scales of the sliced products (in-kernel digits)
   void* ozt_scratch = nullptr;  // scales and digit images of the digitize-once sliced products
+  bool can_slice(int n) const {
+    return ozt_scratch ? oz_supported(n) : (oz_scratch != nullptr && oz_inkernel_supported(n));
+  }
   cudaError_t sliced(const GemmArgs& g) {
     return ozt_scratch ? zgemm_ozt(g, ozt_scratch, ctx->d_err, s) : zgemm_oz(g, oz_scratch, ctx->d_err, s);
   }
@@ -286,7 +289,7 @@ struct Engine {
     const double bytes = 16.0 * nn * units * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
     cudaError_t e;
     const bool masked = active != nullptr;   // masked launches do an unknown share of the work
-    if (mixed == 1 && oz_supported(n) && (oz_scratch || ozt_scratch)) {
+    if (mixed == 1 && can_slice(n)) {
       begin(masked ? K_OTHER : K_GEMM_OZ);
       e = sliced(g);
     } else if (mixed == 2 && tc_supported(n)) {
@@ -323,7 +326,7 @@ struct Engine {
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
       r.n = n; r.units = units; r.active = nullptr;
       // M X with FP64-class accuracy: the sliced tensor-core product, else FP64 FMA
-      if (mixed == 1 && oz_supported(n) && (oz_scratch || ozt_scratch)) {
+      if (mixed == 1 && can_slice(n)) {
         begin(K_GEMM_OZ);
         e = sliced(r);
       } else {

@@ -104,7 +104,8 @@ bool tc_supported(int n);
 // FP64-class complex GEMM on the BF16 tensor cores (exact-accumulation digit slices);
 // `scratch` holds oz_scratch_bytes(n, units) bytes of per-row/column scales
 cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
-bool oz_supported(int n);
+bool oz_supported(int n);            // the digitize-once products (16 <= n <= 512)
+bool oz_inkernel_supported(int n);   // the in-kernel-digit product zgemm_oz (16 <= n <= 256)
 size_t oz_scratch_bytes(int n, int units);
 // the same product with each operand digitized once into global memory and streamed to
 // the tensor cores by bulk copies; `scratch` holds ozt_scratch_bytes(n, units) bytes

@@ -64,7 +64,7 @@ extern "C" negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t
     negf_set_error_message("negf_block_gemm_noalloc: bad stride");
     return NEGF_ERR_ARG;
   }
-  const bool sliced = oz_supported(n);
+  const bool sliced = oz_inkernel_supported(n);
   if (sliced && oz_scratch_bytes(n, units) > kNoAllocScratchBytes) {
     negf_set_error_message(("negf_block_gemm_noalloc: 2 * n * units * 4 = " +
                             std::to_string(oz_scratch_bytes(n, units)) + " bytes of scale scratch exceed the " +

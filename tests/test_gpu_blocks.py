@@ -37,7 +37,7 @@ def _op(x, op):
 GEMM_TOL = {"FP64": 1e-13, "MIXED": 1e-13, "MIXED_TF32": 2e-6}
 
 
-@pytest.mark.parametrize("n", [1, 8, 16, 33, 64, 100, 128, 130, 192, 256, 300])
+@pytest.mark.parametrize("n", [1, 8, 16, 33, 64, 100, 128, 130, 192, 256, 300, 512])
 @pytest.mark.parametrize("opA,opB", [(0, 0), (2, 0), (0, 2), (2, 2)])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED", "MIXED_TF32"])
 def test_block_gemm(P, ctx, n, opA, opB, prec):
