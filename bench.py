@@ -513,6 +513,110 @@ def run_probe(args):
     ctx.close()
 
 
+def run_workload(args):
+    """Mixed vs FP64 on the other workloads (not the headline line): --workload config4 runs
+    the nb = 32, b = 512 device with block-diagonal scattering over `ne` energies;
+    --workload config3 runs the first `devices` devices of the uneven batch (every energy).
+    Times OBC + G^R/G^< sweeps in mixed precision over the whole set, then the FP64 sweeps
+    on a sample of `fp64_sample` energies per device with the same Sigma, and reports the
+    normwise error of the mixed G^R, G^< against FP64 over the BT pattern."""
+    import torch
+    import paper_2602_03438_gb300 as P
+    torch.cuda.set_device(0)
+    # the outputs stay resident: config 4 keeps 628 MB of blocks per energy, config 3's
+    # largest devices 640 MB, so the energies are capped to fit the GPU's memory
+    if args.workload == "config4":
+        full = W.config4()
+        devs = [full.truncated(energies=np.linspace(0, full.ne - 1, args.ne_cap).round().astype(int))]
+    else:
+        shapes = W.config3_shapes()
+        devs = []
+        for k in range(args.devices):
+            d = W.config3_device(k, shapes)
+            devs.append(d.truncated(energies=np.linspace(0, d.ne - 1, min(args.ne_cap, d.ne)).round().astype(int)))
+    ctx = P.Context(0, int(args.workspace_gb * (1 << 30)))
+    sys_ = P.upload(devs)
+    out = P.allocate_outputs(sys_)
+    sc = P.Scattering.from_devices(devs) if devs[0].sigR_scat is not None else None
+    fL = torch.from_numpy(np.concatenate([d.f_L() for d in devs])).cuda()
+    fR = torch.from_numpy(np.concatenate([d.f_R() for d in devs])).cuda()
+    ne_tot = sum(d.ne for d in devs)
+
+    def step():
+        P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"], prec=P.MIXED)
+        P.negf_rgf_lesser(ctx, sys_, P.MIXED, out["sigma_L"], out["sigma_R"], fL, fR, sc, out["GR_diag"],
+                          out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
+
+    step()
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the first run")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # FP64 sweeps on a sample of each device's energies, given the mixed run's Sigma
+    L = sys_.layout()
+    subs, idx_all = [], []
+    for d, dev in enumerate(devs):
+        k = min(args.fp64_sample, dev.ne)
+        idx = np.linspace(0, dev.ne - 1, k).round().astype(int)
+        subs.append(dev.truncated(energies=idx))
+        idx_all.append((d, idx))
+    s2 = P.upload(subs)
+    o2 = P.allocate_outputs(s2)
+    L2 = s2.layout()
+    for (d, idx), sub in zip(idx_all, subs):
+        b = sub.b
+        for j, e in enumerate(idx):
+            src = slice(int(L[d][3] + e * b * b), int(L[d][3] + (e + 1) * b * b))
+            dst = slice(int(L2[d][3] + j * b * b), int(L2[d][3] + (j + 1) * b * b))
+            o2["sigma_L"][dst] = out["sigma_L"][src]
+            o2["sigma_R"][dst] = out["sigma_R"][src]
+    sc2 = P.Scattering.from_devices(subs) if subs[0].sigR_scat is not None else None
+    f2L = torch.from_numpy(np.concatenate([d.f_L() for d in subs])).cuda()
+    f2R = torch.from_numpy(np.concatenate([d.f_R() for d in subs])).cuda()
+    torch.cuda.synchronize()
+    e0.record()
+    P.negf_rgf_lesser(ctx, s2, P.FP64, o2["sigma_L"], o2["sigma_R"], f2L, f2R, sc2, o2["GR_diag"], o2["GR_up"],
+                      o2["GR_low"], o2["GL_diag"], o2["GL_low"], o2["status"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    n64 = sum(len(i) for _, i in idx_all)
+    err = {"G^R": 0.0, "G^<": 0.0}
+    for (d, idx), sub in zip(idx_all, subs):
+        nb, b = sub.nb, sub.b
+        for gname, keys in (("G^R", (("GR_diag", nb), ("GR_up", nb - 1), ("GR_low", nb - 1))),
+                            ("G^<", (("GL_diag", nb), ("GL_low", nb - 1)))):
+            for j, e in enumerate(idx):
+                num = den = 0.0
+                for key, nblk in keys:
+                    if nblk == 0:
+                        continue
+                    off = 4 if key.endswith("diag") else 5
+                    a0 = int(L[d][off] + e * nblk * b * b)
+                    b0 = int(L2[d][off] + j * nblk * b * b)
+                    got = out[key][a0:a0 + nblk * b * b].view(nblk, -1)
+                    ref = o2[key][b0:b0 + nblk * b * b].view(nblk, -1)
+                    num = max(num, float(torch.linalg.vector_norm(got - ref, dim=1).max()))
+                    den = max(den, float(torch.linalg.vector_norm(ref, dim=1).max()))
+                err[gname] = max(err[gname], num / max(den, 1e-300))
+    line = {"workload": args.workload, "devices": len(devs), "energies": ne_tot,
+            "block_sizes": sorted(set(d.b for d in devs)),
+            "mixed": {"value": ne_tot / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+                      "what": "OBC + G^R/G^< sweeps, mixed precision, every energy"},
+            "fp64_sweeps": {"value": n64 / (ms64 / 1e3), "unit": UNIT, "energies": n64},
+            "err_vs_fp64": err,
+            "status": {"obc_not_converged": int((out["obc_status"] != 0).sum().item()),
+                       "rgf_flagged": int((out["status"] != 0).sum().item())}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,9 +634,14 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe", choices=["gemm", "inverse"], default=None)
+    ap.add_argument("--workload", choices=["config3", "config4"], default=None)
+    ap.add_argument("--devices", type=int, default=16)
+    ap.add_argument("--ne-cap", type=int, default=64)
     args = ap.parse_args(argv)
     if args.probe:
         run_probe(args)
+    elif args.workload:
+        run_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
