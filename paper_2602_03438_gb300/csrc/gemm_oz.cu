@@ -945,11 +945,52 @@ __device__ __forceinline__ void mma_bf16_n32(uint32_t tmem_d, uint64_t a, uint64
       : "memory");
 }
 
+// column scales of op(B) of unit u for n <= 128, by one CTA of 256 threads: the
+// columns of B (op N, two threads per column over alternate rows) or the rows of B
+// (op H, a warp per row)
+__device__ __forceinline__ void b_col_scales(const GemmArgs& g, int u, int* eb) {
+  const int n = g.n;
+  const zc* B = g.B.at(u);
+  int* out = eb + (size_t)u * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (g.opB == OP_H) {
+    for (int r = warp; r < n; r += 8) {
+      double v = 0.0;
+      for (int k = lane; k < n; k += 32) {
+        const zc x = B[(size_t)r * n + k];
+        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+      }
+      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+      if (lane == 0) out[r] = scale_exp(v);
+    }
+  } else {
+    __shared__ double bpart[2][128];
+    const int c = tid & 127, h = tid >> 7;
+    double v = 0.0;
+    if (c < n) {
+#pragma unroll 8
+      for (int k = h; k < n; k += 2) {
+        const zc x = B[(size_t)k * n + c];
+        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+      }
+    }
+    bpart[h][c] = v;
+    __syncthreads();
+    if (tid < n) out[tid] = scale_exp(fmax(bpart[0][tid], bpart[1][tid]));
+  }
+}
+
 // A operand digit images for the half-width tiles: one CTA per (64 rows, unit); each
-// thread owns a row and 2 consecutive complex k of every 8-complex chunk
-__global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImages im) {
+// thread owns a row and 2 consecutive complex k of every 8-complex chunk.  With
+// `with_b` (n <= 128) the last CTA of each unit computes op(B)'s column scales instead,
+// so that both pre-passes share one launch.
+__global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImages im, int with_b) {
   const int u = blockIdx.y;
   if (g.active && !g.active[u]) return;
+  if (with_b && blockIdx.x == gridDim.x - 1) {
+    b_col_scales(g, u, im.eb);
+    return;
+  }
   constexpr int RB = 64;
   const int n = g.n, r0 = blockIdx.x * RB, tm = r0 / TM;
   const zc* A = g.A.at(u);
@@ -1530,11 +1571,10 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.eb = im.ea + (size_t)n * g.units;
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
-  oz_digitize_a2_kernel<<<dim3(im.tiles_m * (TM / 64), g.units), 256, 0, s>>>(g, im);
+  // A digit images and op(B)'s column scales in one launch (n <= 96 here)
+  oz_digitize_a2_kernel<<<dim3(im.tiles_m * (TM / 64) + 1, g.units), 256, 0, s>>>(g, im, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
                        (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
                           ? 1 : 0;
@@ -1594,11 +1634,10 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.eb = im.ea + (size_t)n * g.units;
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
-  oz_digitize_a2_kernel<<<dim3(TM / 64, g.units), 256, 0, s>>>(g, im);
+  // A digit images and op(B)'s column scales in one launch
+  oz_digitize_a2_kernel<<<dim3(TM / 64 + 1, g.units), 256, 0, s>>>(g, im, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
                        (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
                           ? 1 : 0;

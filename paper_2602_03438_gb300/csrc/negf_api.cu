@@ -146,18 +146,47 @@ struct AsmArgs {
   const double *fL, *fR;           // this device's occupations (nullable unless SigL)
 };
 
-__global__ void assemble_kernel(AsmArgs a) {
+// One 32 x 32 tile of every requested block per CTA (32 x 8 threads, 4 rows each);
+// the conjugate-transposed terms (A_{j+1,j}, the lead Gamma's Sigma^H) are read as the
+// transposed tile through shared memory, so that every global access is a row segment.
+constexpr int ASM_T = 32;
+
+__global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const int u = blockIdx.y;
   const int b = a.dv.b, nb = a.dv.nb;
   const long long bb = (long long)b * b;
   const int e = a.e0 + u;
   const zc z = zmake(a.dv.E[e], a.dv.eta);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < bb;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / b), c = (int)(idx - (long long)r * b);
-    const long long rc = idx, cr = (long long)c * b + r;
+  const int ntile = (b + ASM_T - 1) / ASM_T;
+  const int r0 = (blockIdx.x / ntile) * ASM_T, c0 = (blockIdx.x % ntile) * ASM_T;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ zc tS[ASM_T][ASM_T + 1], tH[ASM_T][ASM_T + 1];
+  const int i = a.i_diag, j = a.i_off;
+  const bool lead_lesser = a.SigL && (i == 0 || i == nb - 1);
+  const zc* sg = (i == 0) ? a.sigma_L + e * bb : a.sigma_R + e * bb;
+  const double fo = (i == 0) ? (a.fL ? a.fL[e] : 0.0) : (a.fR ? a.fR[e] : 0.0);
+  // transposed tiles: (row c0 + ty + 8k, column r0 + tx) of S_up, H_up (for A_{j+1,j}) and
+  // of the lead Sigma (for Sigma^H), stored as [tx][ty + 8k]
+  if (a.Alow) {
+#pragma unroll
+    for (int k = 0; k < ASM_T / 8; ++k) {
+      const int rr = c0 + ty + 8 * k, cc = r0 + tx;
+      zc sv = zmake(0.0, 0.0), hv = zmake(0.0, 0.0);
+      if (rr < b && cc < b) {
+        if (a.dv.Su) sv = a.dv.Su[j * bb + (long long)rr * b + cc];
+        hv = a.dv.Hu[j * bb + (long long)rr * b + cc];
+      }
+      tS[tx][ty + 8 * k] = sv;
+      tH[tx][ty + 8 * k] = hv;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < ASM_T / 8; ++k) {
+    const int r = r0 + ty + 8 * k, c = c0 + tx;
+    if (r >= b || c >= b) continue;
+    const long long rc = (long long)r * b + c;
     if (a.Adiag) {
-      const int i = a.i_diag;
       zc s = a.dv.Sd ? a.dv.Sd[i * bb + rc] : zmake(r == c ? 1.0 : 0.0, 0.0);
       zc v = zsub(zmul(z, s), a.dv.Hd[i * bb + rc]);
       if (a.sc.sigR) v = zsub(v, a.sc.sigR[e * a.sc.e_stride + i * bb + rc]);
@@ -165,42 +194,53 @@ __global__ void assemble_kernel(AsmArgs a) {
       if (i == nb - 1) v = zsub(v, a.sigma_R[e * bb + rc]);
       a.Adiag[u * bb + rc] = v;
     }
-    if (a.SigL) {
-      const int i = a.i_diag;
-      zc v = zmake(0.0, 0.0);
-      if (a.sc.sigL) {
-        const double f = a.sc.scale ? a.sc.scale[(long long)e * nb + i] : 1.0;
-        v = zscale(a.sc.sigL[e * a.sc.e_stride + i * bb + rc], f);
-      }
-      // lead lesser i f Gamma = -f (Sigma - Sigma^H)
-      if (i == 0) {
-        const zc d = zsub(a.sigma_L[e * bb + rc], zconj(a.sigma_L[e * bb + cr]));
-        v = zsub(v, zscale(d, a.fL[e]));
-      }
-      if (i == nb - 1) {
-        const zc d = zsub(a.sigma_R[e * bb + rc], zconj(a.sigma_R[e * bb + cr]));
-        v = zsub(v, zscale(d, a.fR[e]));
-      }
-      a.SigL[u * bb + rc] = v;
-    }
     if (a.Aup) {   // A_{j,j+1} = z S_up - H_up
-      const int j = a.i_off;
       zc s = a.dv.Su ? a.dv.Su[j * bb + rc] : zmake(0.0, 0.0);
       a.Aup[u * bb + rc] = zsub(zmul(z, s), a.dv.Hu[j * bb + rc]);
     }
-    if (a.Alow) {  // A_{j+1,j} = z S_up^H - H_up^H
-      const int j = a.i_off;
-      zc s = a.dv.Su ? zconj(a.dv.Su[j * bb + cr]) : zmake(0.0, 0.0);
-      a.Alow[u * bb + rc] = zsub(zmul(z, s), zconj(a.dv.Hu[j * bb + cr]));
+    if (a.Alow) {  // A_{j+1,j} = z S_up^H - H_up^H: element (r, c) = conj of (c, r)
+      const zc s = zconj(tS[ty + 8 * k][tx]);
+      a.Alow[u * bb + rc] = zsub(zmul(z, s), zconj(tH[ty + 8 * k][tx]));
     }
+  }
+  if (!a.SigL) return;
+  __syncthreads();
+  if (lead_lesser) {   // transposed tile of this lead's Sigma for its Sigma^H
+#pragma unroll
+    for (int k = 0; k < ASM_T / 8; ++k) {
+      const int rr = c0 + ty + 8 * k, cc = r0 + tx;
+      tS[tx][ty + 8 * k] = (rr < b && cc < b) ? sg[(long long)rr * b + cc] : zmake(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < ASM_T / 8; ++k) {
+    const int r = r0 + ty + 8 * k, c = c0 + tx;
+    if (r >= b || c >= b) continue;
+    const long long rc = (long long)r * b + c;
+    zc v = zmake(0.0, 0.0);
+    if (a.sc.sigL) {
+      const double f = a.sc.scale ? a.sc.scale[(long long)e * nb + i] : 1.0;
+      v = zscale(a.sc.sigL[e * a.sc.e_stride + i * bb + rc], f);
+    }
+    // lead lesser i f Gamma = -f (Sigma - Sigma^H)
+    if (lead_lesser) {
+      const zc d = zsub(sg[rc], zconj(tS[ty + 8 * k][tx]));
+      v = zsub(v, zscale(d, fo));
+      if (nb == 1) {   // both leads on the one block
+        const zc* sg2 = a.sigma_R + e * bb;
+        const zc d2 = zsub(sg2[rc], zconj(sg2[(long long)c * b + r]));
+        v = zsub(v, zscale(d2, a.fR ? a.fR[e] : 0.0));
+      }
+    }
+    a.SigL[u * bb + rc] = v;
   }
 }
 
 cudaError_t assemble(const AsmArgs& a, cudaStream_t s) {
   if (a.units <= 0) return cudaSuccess;
-  const long long bb = (long long)a.dv.b * a.dv.b;
-  dim3 grid((unsigned)std::min<long long>((bb + 255) / 256, 1024), a.units);
-  assemble_kernel<<<grid, 256, 0, s>>>(a);
+  const int nt = (a.dv.b + ASM_T - 1) / ASM_T;
+  assemble_kernel<<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
   return cudaGetLastError();
 }
 
