@@ -197,12 +197,35 @@ __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n
     //    the pivot column entering as 0 (so that it becomes -f_r / d)
     if (upd) {
       const C pc = prow[mc];
-      for (int r = r0; r < n; r += rs) {
+      const C zero = cmk<R>((R)0, (R)0);
+      const C kr = krow[mc];
+      int r = r0;
+      // four rows per iteration: their loads are independent and issued together (FP32;
+      // the FP64 matrix of b = 128 lives in global scratch, where this did not pay)
+      if (sizeof(R) == 4)
+      for (; r + 3 * rs < n; r += 4 * rs) {
+        C w[4], f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rq = r + q * rs;
+          w[q] = (mc == k) ? zero : ((rq == p) ? kr : W[(size_t)rq * ld + mc]);
+          f[q] = fcol[rq];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rq = r + q * rs;
+          C x = w[q];
+          x.x = x.x - (f[q].x * pc.x - f[q].y * pc.y);
+          x.y = x.y - (f[q].x * pc.y + f[q].y * pc.x);
+          W[(size_t)rq * ld + mc] = (rq == k) ? pc : x;
+        }
+      }
+      for (; r < n; r += rs) {
         const size_t i = (size_t)r * ld + mc;
         if (r == k) {
           W[i] = pc;
         } else {
-          C w = (mc == k) ? cmk<R>((R)0, (R)0) : ((r == p) ? krow[mc] : W[i]);
+          C w = (mc == k) ? zero : ((r == p) ? kr : W[i]);
           const C f = fcol[r];
           w.x = w.x - (f.x * pc.x - f.y * pc.y);
           w.y = w.y - (f.x * pc.y + f.y * pc.x);
