@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n
       const C zero = cmk<R>((R)0, (R)0);
       const C kr = krow[mc];
       int r = r0;
-      // four rows per iteration: their loads are independent and issued together (FP32;
-      // the FP64 matrix of b = 128 lives in global scratch, where this did not pay)
-      if (sizeof(R) == 4)
+      // four rows per iteration: their loads are independent and issued together (FP32
+      // and n >= 96, where it measured faster; the FP64 matrix of b = 128 lives in
+      // global scratch, and small blocks have few rows per thread)
+      if (sizeof(R) == 4 && n >= 96)
       for (; r + 3 * rs < n; r += 4 * rs) {
         C w[4], f[4];
 #pragma unroll
