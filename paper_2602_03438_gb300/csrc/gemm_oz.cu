@@ -43,7 +43,6 @@ constexpr int NR = 2 * TNC;             // real MMA columns (64)
 constexpr int KC = 16;                  // complex K per chunk
 constexpr int NS = 8;                   // digits per value
 constexpr int NG = 8;                   // scale groups d = 2..9
-constexpr int NPAIR = NS * (NS + 1) / 2;   // slice pairs with s + t <= NS + 1
 constexpr int HSPLIT = 4;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
 constexpr int NT = 256;
 constexpr int kCluster = 4;            // column tiles sharing one A tile's digits
@@ -591,7 +590,6 @@ __global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const 
 // issues the MMAs from one thread.
 // ===========================================================================
 constexpr uint32_t A_IMG = NS * A_SLICE;   // one chunk of one 128-row A tile (64 KB)
-constexpr uint32_t B_IMG = NS * B_SLICE;   // one chunk of one 32-column B tile (32 KB)
 
 struct OzImages {
   unsigned char* a;   // [unit][tiles_m][nchunks] images of A_IMG bytes
@@ -682,12 +680,6 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// bulk copy global -> this CTA's shared memory, completion counted on `bar`
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
 }
 // bulk copy global -> the same shared offset of every member in `mask`, counted on each
 // member's barrier at the same offset
@@ -934,16 +926,6 @@ __device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
   return d;
 }
 
-// kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128, N = 32
-constexpr uint32_t IDESC2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR2 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16_n32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC2), "r"(acc)
-      : "memory");
-}
 
 // column scales of op(B) of unit u for n <= 128, by one CTA of 256 threads: the
 // columns of B (op N, two threads per column over alternate rows) or the rows of B
