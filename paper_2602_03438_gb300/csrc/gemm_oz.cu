@@ -962,10 +962,17 @@ __device__ __forceinline__ void b_col_scales(const GemmArgs& g, int u, int* eb) 
   }
 }
 
-// A operand digit images for the half-width tiles: one CTA per (64 rows, unit); each
-// thread owns a row and 2 consecutive complex k of every 8-complex chunk.  With
-// `with_b` (n <= 128) the last CTA of each unit computes op(B)'s column scales instead,
-// so that both pre-passes share one launch.
+// A operand digit images of the 32-byte-swizzled layouts (n <= 128, one row tile): one
+// CTA per (32 rows, unit), eight threads per row.  Image rows n..127 are left as they
+// are: an output row depends on its own A row only, and rows >= n are never stored.
+// Thread (row, sub) keeps the two complex k 2 (sub & 3), +1 of every chunk c with
+// c = sub >> 2 (mod 2) in registers: the row's scale is the maximum over the eight
+// threads (shuffles within the group), and the digits are made from the same
+// registers, so A is read from memory once.  With
+// `with_b` the last CTA of each unit computes op(B)'s column scales instead, so that
+// both pre-passes share one launch.
+constexpr int PRE_ROWS = 32;
+constexpr int PRE_OWN = 8;   // chunks owned per thread: n <= 2 * PRE_OWN * KC2 = 128
 __global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImages im, int with_b) {
   const int u = blockIdx.y;
   if (g.active && !g.active[u]) return;
@@ -973,59 +980,45 @@ __global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImage
     b_col_scales(g, u, im.eb);
     return;
   }
-  constexpr int RB = 64;
-  const int n = g.n, r0 = blockIdx.x * RB, tm = r0 / TM;
-  const zc* A = g.A.at(u);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  __shared__ int es[RB];
-  __shared__ double part[4][RB];
-  // ---- row scales of op(A): rows of A (op N, a warp per row) or columns of A (op H)
-  if (g.opA == OP_N) {
-    for (int r = warp; r < RB; r += 8) {
-      const int gm = r0 + r;
-      double v = 0.0;
-      if (gm < n)
-        for (int k = lane; k < n; k += 32) {
-          const zc x = A[(size_t)gm * n + k];
-          v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
-        }
-      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
-      if (lane == 0) es[r] = scale_exp(v);
-    }
-  } else {
-    const int r = tid & 63, ks = tid >> 6, gm = r0 + r;
-    double v = 0.0;
-    if (gm < n)
-      for (int k = ks; k < n; k += 4) {
-        const zc x = A[(size_t)k * n + gm];
-        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
-      }
-    part[ks][r] = v;
-    __syncthreads();
-    if (tid < RB) {
-      double w = 0.0;
-      for (int q = 0; q < 4; ++q) w = fmax(w, part[q][tid]);
-      es[tid] = scale_exp(w);
+  const int n = g.n, nchunks = im.nchunks;
+  const zc* __restrict__ A = g.A.at(u);
+  const int tid = threadIdx.x, sub = tid & 7;
+  const int gm = blockIdx.x * PRE_ROWS + (tid >> 3), tm = gm / TM, am = gm - tm * TM;
+  const int ak = (sub & 3) * 2, c0 = sub >> 2;
+  zc v[PRE_OWN][2];
+#pragma unroll
+  for (int j = 0; j < PRE_OWN; ++j) {
+    const int c = c0 + 2 * j;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gk = c * KC2 + ak + h;
+      zc x = zmake(0.0, 0.0);
+      if (c < nchunks && gm < n && gk < n) x = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+      v[j][h] = x;
     }
   }
-  __syncthreads();
-  if (tid < RB && r0 + tid < n) im.ea[(size_t)u * n + r0 + tid] = es[tid];
-  const int rl = tid >> 2, ak = (tid & 3) * 2, gm = r0 + rl, am = gm - tm * TM;
-  const int e = es[rl];
-  for (int c = 0; c < im.nchunks; ++c) {
-    const int k0 = c * KC2;
+  double mx = 0.0;
+#pragma unroll
+  for (int j = 0; j < PRE_OWN; ++j)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) mx = fmax(mx, fmax(fabs(v[j][h].x), fabs(v[j][h].y)));
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const int e = scale_exp(mx);
+  if (sub == 0 && gm < n) im.ea[(size_t)u * n + gm] = e;
+#pragma unroll
+  for (int j = 0; j < PRE_OWN; ++j) {
+    const int c = c0 + 2 * j;
+    if (c >= nchunks) break;
     unsigned int pr[NS], pi[NS];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gk = k0 + ak + j;
-      zc v = zmake(0.0, 0.0);
-      if (gm < n && gk < n) v = (g.opA == OP_N) ? A[(size_t)gm * n + gk] : zconj(A[(size_t)gk * n + gm]);
+    for (int h = 0; h < 2; ++h) {
       int dr[NS], di[NS];
-      digits(v.x, e, dr);
-      digits(v.y, e, di);
+      digits(v[j][h].x, e, dr);
+      digits(v[j][h].y, e, di);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
-        if (j) {
+        if (h) {
           pr[q] |= bf16_of_int(dr[q]) << 16;
           pi[q] |= bf16_of_int(di[q]) << 16;
         } else {
@@ -1034,7 +1027,7 @@ __global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImage
         }
       }
     }
-    unsigned char* img = im.a + ((size_t)(u * im.tiles_m + tm) * im.nchunks + c) * A_IMG2;
+    unsigned char* img = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks + c) * A_IMG2;
     const uint32_t o_r = sw32(am, ak), o_i = sw32(am, KC2 + ak);
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
@@ -1554,7 +1547,7 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
   // A digit images and op(B)'s column scales in one launch (n <= 96 here)
-  oz_digitize_a2_kernel<<<dim3(im.tiles_m * (TM / 64) + 1, g.units), 256, 0, s>>>(g, im, 1);
+  oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
@@ -1617,7 +1610,7 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
   // A digit images and op(B)'s column scales in one launch
-  oz_digitize_a2_kernel<<<dim3(TM / 64 + 1, g.units), 256, 0, s>>>(g, im, 1);
+  oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
