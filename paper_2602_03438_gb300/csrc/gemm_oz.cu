@@ -1317,8 +1317,9 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
     }
   } else if (warp >= 8) {
     // ---------------- B digits: column bn, complex k = bk of every chunk (neighbouring lanes
-    // hold k and k+1 and are joined by a shuffle); the next chunk's value (of this unit
-    // or the next) is loaded while this one is digitized
+    // hold k and k+1 and are joined by a shuffle).  The next chunk's value (of this unit
+    // or the next) is loaded while this one is digitized, a unit's column scale when its
+    // first chunk is loaded, and the digits are made before waiting for the stage.
     const int tb = tid - 256, bn = tb >> 3, bk = tb & 7, gn = n0 + bn;
     const uint32_t o1 = sw32(bn, bk), o2 = sw32(bn, KCP + bk), o3 = sw32(TNC + bn, bk), o4 = sw32(TNC + bn, KCP + bk);
     auto next_unit = [&](int u) {
@@ -1333,42 +1334,58 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
       if (gn < n && gk < n) r = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
       return r;
     };
+    auto load_eb = [&](int u) { return (gn < n) ? im.eb[(size_t)u * n + gn] : 0; };
     int u = cid;
     if (u < g.units && skip(u)) u = next_unit(u);
     int c = 0;
     zc rb = zmake(0.0, 0.0);
-    if (u < g.units) rb = load1(u, 0);
+    int eb_cur = 0, eb_nxt = 0;
+    if (u < g.units) {
+      rb = load1(u, 0);
+      eb_cur = load_eb(u);
+    }
     uint32_t cg = 0;
     while (u < g.units && !s_fail) {
-      const int eb_n = (gn < n) ? im.eb[(size_t)u * n + gn] : 0;
       const zc cur = rb;
       int u2 = u, c2 = c + 1;
       if (c2 == nchunks) { c2 = 0; u2 = next_unit(u); }
-      if (u2 < g.units) rb = load1(u2, c2);
+      if (u2 < g.units) {
+        rb = load1(u2, c2);
+        if (c2 == 0) eb_nxt = load_eb(u2);
+      }
+      // B'^T rows: row bn = [Re | -Im], row TNC + bn = [Im | Re]; lane pairs (k, k+1)
+      unsigned int pr[NS], pi[NS];
+      {
+        int dr[NS], di[NS];
+        digits(cur.x, eb_cur, dr);
+        digits(cur.y, eb_cur, di);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          const unsigned int r0v = bf16_of_int(dr[q]), i0v = bf16_of_int(di[q]);
+          const unsigned int r1v = __shfl_down_sync(0xffffffffu, r0v, 1);
+          const unsigned int i1v = __shfl_down_sync(0xffffffffu, i0v, 1);
+          pr[q] = r0v | (r1v << 16);
+          pi[q] = i0v | (i1v << 16);
+        }
+      }
       const int st = cg & 1;
       if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
-      int dr[NS], di[NS];
-      digits(cur.x, eb_n, dr);
-      digits(cur.y, eb_n, di);
-      unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
+      if ((bk & 1) == 0) {
+        unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        const unsigned int r0v = bf16_of_int(dr[q]), i0v = bf16_of_int(di[q]);
-        const unsigned int r1v = __shfl_down_sync(0xffffffffu, r0v, 1);
-        const unsigned int i1v = __shfl_down_sync(0xffffffffu, i0v, 1);
-        if ((bk & 1) == 0) {   // B'^T: row bn: [Re | -Im];  row TNC+bn: [Im | Re]
-          const unsigned int pr = r0v | (r1v << 16), pi = i0v | (i1v << 16);
+        for (int q = 0; q < NS; ++q) {
           unsigned char* P = Bsl + q * B_SLICE_P;
-          *reinterpret_cast<unsigned int*>(P + o1) = pr;
-          *reinterpret_cast<unsigned int*>(P + o2) = pi ^ 0x80008000u;
-          *reinterpret_cast<unsigned int*>(P + o3) = pi;
-          *reinterpret_cast<unsigned int*>(P + o4) = pr;
+          *reinterpret_cast<unsigned int*>(P + o1) = pr[q];
+          *reinterpret_cast<unsigned int*>(P + o2) = pi[q] ^ 0x80008000u;
+          *reinterpret_cast<unsigned int*>(P + o3) = pi[q];
+          *reinterpret_cast<unsigned int*>(P + o4) = pr[q];
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_local(&full[st]);
       ++cg;
+      if (c2 == 0) eb_cur = eb_nxt;
       u = u2;
       c = c2;
     }
