@@ -219,9 +219,11 @@ __device__ __forceinline__ int scale_exp(double v) {
 }
 
 // digits of x at scale 2^e (|x| < 2^(e-1)): X = rint(|x| 2^(7 NS - e)) <= 2^55 is cut
-// into base-2^7 fields from the least significant one up, each carried into a
-// balanced digit (|d| <= 64); d[0] is the most significant, and the sign of x is
-// applied to every digit
+// into balanced base-2^7 digits (|d| <= 64), d[0] the most significant, and the sign of
+// x is applied to every digit.  Adding 64 to each of the NS - 1 low fields lets binary
+// carries do the balancing: field k of Y = X + 64 sum_k 2^(7k) is f_k + c_(k-1) + 64
+// mod 128 with carry c_k = [f_k + c_(k-1) >= 64], so d_k = field_k(Y) - 64, and the top
+// digit is Y >> 7 (NS - 1) = f_(NS-1) + c_(NS-2)
 __device__ __forceinline__ void digits(double x, int e, int d[NS]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
@@ -232,8 +234,9 @@ __device__ __forceinline__ void digits(double x, int e, int d[NS]) {
     if (rs <= 0) X = mant << (-rs);
     else if (rs < 64) X = (mant + (1ull << (rs - 1))) >> rs;
   }
-  const unsigned int lo = (unsigned int)X, hi = (unsigned int)(X >> 32);
-  int carry = 0;
+  static_assert(NS == 8, "the balancing constant holds 64 in each of seven 7-bit fields");
+  const unsigned long long Y = X + 0x0001020408102040ull;
+  const unsigned int lo = (unsigned int)Y, hi = (unsigned int)(Y >> 32);
 #pragma unroll
   for (int k = 0; k < NS - 1; ++k) {
     const int sh = 7 * k;
@@ -241,11 +244,9 @@ __device__ __forceinline__ void digits(double x, int e, int d[NS]) {
     if (sh + 7 <= 32) f = (lo >> sh) & 127u;
     else if (sh >= 32) f = (hi >> (sh - 32)) & 127u;
     else f = __funnelshift_r(lo, hi, sh) & 127u;
-    const int v = (int)f + carry;
-    carry = v >= 64 ? 1 : 0;
-    d[NS - 1 - k] = v - (carry << 7);
+    d[NS - 1 - k] = (int)f - 64;
   }
-  d[0] = (int)(X >> (7 * (NS - 1))) + carry;
+  d[0] = (int)(Y >> (7 * (NS - 1)));
   if (bits >> 63) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) d[k] = -d[k];
@@ -1223,8 +1224,8 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
 // G_2k 2^7 + G_2k+1 (each group sum stays below 2^23 for n <= 128, so a pair stays
 // below 2^31), free TMEM for the next tile, and then recombine the pairs and store D
 // while the next tile's MMAs run.
-// Warps 0-7: epilogue (TMEM lanes 32*(w%4), 16 columns each); 8-15: B digits;
-// 16: A copies; 17: MMA issue.
+// Warps 0-7: epilogue (TMEM lanes 32*(w%4), 16 columns each); 8-11 and 12-15: B digits
+// of the stages of even and odd chunk counts; 16: A copies; 17: MMA issue.
 // ===========================================================================
 constexpr int KCP = 8;                                  // complex K per chunk
 constexpr uint32_t B_SLICE_P = NR * ROWB2;              // 2 KB: 64 B'^T rows of 32 bytes
@@ -1254,8 +1255,8 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
   const int n0 = (int)rank * TNC;
 
   if (tid == 0) {
-    mbar_init(&full[0], 9);   // the A copy (expect_tx) and the eight B warps
-    mbar_init(&full[1], 9);
+    mbar_init(&full[0], 5);   // the A copy (expect_tx) and the four B warps of the stage's group
+    mbar_init(&full[1], 5);
     mbar_init(&empty[0], CL);
     mbar_init(&empty[1], CL);
     mbar_init(done, 1);
@@ -1316,76 +1317,91 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
       }
     }
   } else if (warp >= 8) {
-    // ---------------- B digits: column bn, complex k = bk of every chunk (neighbouring lanes
-    // hold k and k+1 and are joined by a shuffle).  The next chunk's value (of this unit
-    // or the next) is loaded while this one is digitized, a unit's column scale when its
-    // first chunk is loaded, and the digits are made before waiting for the stage.
-    const int tb = tid - 256, bn = tb >> 3, bk = tb & 7, gn = n0 + bn;
-    const uint32_t o1 = sw32(bn, bk), o2 = sw32(bn, KCP + bk), o3 = sw32(TNC + bn, bk), o4 = sw32(TNC + bn, KCP + bk);
+    // ---------------- B digits: warps 8-11 fill the stages of even chunk counts, warps
+    // 12-15 those of odd ones.  A thread owns column bn and the complex pair k = 2 kp,
+    // 2 kp + 1 of its group's chunks (one 4-byte BF16 pair per row and digit plane).  The
+    // group's next chunk (two on, of this unit or the next) is loaded while this one is
+    // digitized, a unit's column scale with the group's first chunk of that unit, and the
+    // digits are made before waiting for the stage.
+    const int grp = (warp - 8) >> 2;
+    const int tb = tid - 256 - 128 * grp, bn = tb >> 2, kp = tb & 3, gn = n0 + bn, k2 = 2 * kp;
+    const uint32_t o1 = sw32(bn, k2), o2 = sw32(bn, KCP + k2), o3 = sw32(TNC + bn, k2), o4 = sw32(TNC + bn, KCP + k2);
     auto next_unit = [&](int u) {
       for (u += ncl; u < g.units && skip(u); u += ncl) {
       }
       return u;
     };
-    auto load1 = [&](int u, int c) -> zc {
+    auto advance = [&](int& u, int& c) {
+      if (++c == nchunks) {
+        c = 0;
+        u = next_unit(u);
+      }
+    };
+    auto load2 = [&](int u, int c, zc& v0, zc& v1) {
       const zc* B = g.B.at(u);
-      const int gk = c * KCP + bk;
-      zc r = zmake(0.0, 0.0);
-      if (gn < n && gk < n) r = (g.opB == OP_N) ? B[(size_t)gk * n + gn] : zconj(B[(size_t)gn * n + gk]);
-      return r;
+      const int gk = c * KCP + k2;
+      v0 = zmake(0.0, 0.0);
+      v1 = zmake(0.0, 0.0);
+      if (gn >= n) return;
+      if (g.opB == OP_N) {
+        if (gk < n) v0 = B[(size_t)gk * n + gn];
+        if (gk + 1 < n) v1 = B[(size_t)(gk + 1) * n + gn];
+      } else {
+        if (gk < n) v0 = zconj(B[(size_t)gn * n + gk]);
+        if (gk + 1 < n) v1 = zconj(B[(size_t)gn * n + gk + 1]);
+      }
     };
     auto load_eb = [&](int u) { return (gn < n) ? im.eb[(size_t)u * n + gn] : 0; };
-    int u = cid;
+    int u = cid, c = 0;
     if (u < g.units && skip(u)) u = next_unit(u);
-    int c = 0;
-    zc rb = zmake(0.0, 0.0);
+    if (grp == 1 && u < g.units) advance(u, c);
+    zc r0 = zmake(0.0, 0.0), r1 = zmake(0.0, 0.0);
     int eb_cur = 0, eb_nxt = 0;
     if (u < g.units) {
-      rb = load1(u, 0);
+      load2(u, c, r0, r1);
       eb_cur = load_eb(u);
     }
-    uint32_t cg = 0;
+    uint32_t cg = (uint32_t)grp;
     while (u < g.units && !s_fail) {
-      const zc cur = rb;
-      int u2 = u, c2 = c + 1;
-      if (c2 == nchunks) { c2 = 0; u2 = next_unit(u); }
+      const zc v0 = r0, v1 = r1;
+      int u2 = u, c2 = c;
+      advance(u2, c2);
+      if (u2 < g.units) advance(u2, c2);
+      const bool new_unit = u2 != u;
       if (u2 < g.units) {
-        rb = load1(u2, c2);
-        if (c2 == 0) eb_nxt = load_eb(u2);
+        load2(u2, c2, r0, r1);
+        if (new_unit) eb_nxt = load_eb(u2);
       }
-      // B'^T rows: row bn = [Re | -Im], row TNC + bn = [Im | Re]; lane pairs (k, k+1)
+      // B'^T rows: row bn = [Re | -Im], row TNC + bn = [Im | Re]
       unsigned int pr[NS], pi[NS];
       {
-        int dr[NS], di[NS];
-        digits(cur.x, eb_cur, dr);
-        digits(cur.y, eb_cur, di);
+        int dr0[NS], di0[NS], dr1[NS], di1[NS];
+        digits(v0.x, eb_cur, dr0);
+        digits(v0.y, eb_cur, di0);
+        digits(v1.x, eb_cur, dr1);
+        digits(v1.y, eb_cur, di1);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-          const unsigned int r0v = bf16_of_int(dr[q]), i0v = bf16_of_int(di[q]);
-          const unsigned int r1v = __shfl_down_sync(0xffffffffu, r0v, 1);
-          const unsigned int i1v = __shfl_down_sync(0xffffffffu, i0v, 1);
-          pr[q] = r0v | (r1v << 16);
-          pi[q] = i0v | (i1v << 16);
+          pr[q] = bf16_of_int(dr0[q]) | (bf16_of_int(dr1[q]) << 16);
+          pi[q] = bf16_of_int(di0[q]) | (bf16_of_int(di1[q]) << 16);
         }
       }
       const int st = cg & 1;
       if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
-      if ((bk & 1) == 0) {
-        unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
+      unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          unsigned char* P = Bsl + q * B_SLICE_P;
-          *reinterpret_cast<unsigned int*>(P + o1) = pr[q];
-          *reinterpret_cast<unsigned int*>(P + o2) = pi[q] ^ 0x80008000u;
-          *reinterpret_cast<unsigned int*>(P + o3) = pi[q];
-          *reinterpret_cast<unsigned int*>(P + o4) = pr[q];
-        }
+      for (int q = 0; q < NS; ++q) {
+        unsigned char* P = Bsl + q * B_SLICE_P;
+        *reinterpret_cast<unsigned int*>(P + o1) = pr[q];
+        *reinterpret_cast<unsigned int*>(P + o2) = pi[q] ^ 0x80008000u;
+        *reinterpret_cast<unsigned int*>(P + o3) = pi[q];
+        *reinterpret_cast<unsigned int*>(P + o4) = pr[q];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_local(&full[st]);
-      ++cg;
-      if (c2 == 0) eb_cur = eb_nxt;
+      cg += 2;
+      if (new_unit) eb_cur = eb_nxt;
       u = u2;
       c = c2;
     }

@@ -378,6 +378,14 @@ struct Engine {
       ++ctx->launches;
       one_minus_kernel<<<grid, 256, 0, s>>>(T1, n);                        // I - M X
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (mixed == 1 && ozt_scratch && oz_supported(n)) {
+        // X <- X + X (I - M X) in one product: these kernels read op(A) only through the
+        // digit images made before they start, and C and D element by element in one
+        // thread, so D, A and C may all be X
+        if ((e = gemm(X, X, OP_N, T1, OP_N, zmake(1.0, 0.0), X, zmake(1.0, 0.0), n, units)) != cudaSuccess)
+          return e;
+        continue;
+      }
       if ((e = gemm(T2, X, OP_N, T1, OP_N, zmake(1.0, 0.0), BMat{nullptr, 0}, zmake(0.0, 0.0), n, units)) !=
           cudaSuccess)
         return e;                                                          // X (I - M X)
