@@ -682,6 +682,10 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global address
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // bulk copy global -> the same shared offset of every member in `mask`, counted on each
 // member's barrier at the same offset
 __device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
@@ -1280,18 +1284,34 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
 
   if (warp == 16) {
     // ---------------- A: this member's quarter of each chunk's digit image, multicast
+    // (this member's part of the image PF_A chunks ahead, of this unit or the next, is
+    // prefetched into L2 when a chunk is copied, so that the copies, which wait for a free
+    // stage, read L2 rather than DRAM)
     if (lane == 0) {
       constexpr uint32_t APART = A_IMG2 / CL;
+      constexpr int PF_A = 4;
+      const size_t unit_img = (size_t)im.tiles_m * nchunks * A_IMG2;
       uint32_t cg = 0;
+      bool first = true;
       for (int u = cid; u < g.units && !s_fail; u += ncl) {
         if (skip(u)) continue;
-        const unsigned char* aimg = im.a + (size_t)u * im.tiles_m * nchunks * A_IMG2;
+        int un = u + ncl;
+        while (un < g.units && skip(un)) un += ncl;
+        const unsigned char* aimg = im.a + (size_t)u * unit_img;
+        if (first) {   // the first unit's first chunks
+          for (int c = 0; c < PF_A && c < nchunks; ++c) prefetch_l2(aimg + (size_t)c * A_IMG2 + rank * APART, APART);
+          first = false;
+        }
         for (int c = 0; c < nchunks; ++c, ++cg) {
           const int st = cg & 1;
           if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
           mbar_expect_tx(&full[st], A_IMG2);
           bulk_g2s_multicast(lbase + st * STAGE_P + rank * APART, aimg + (size_t)c * A_IMG2 + rank * APART, APART,
                              &full[st], (uint16_t)((1u << CL) - 1u));
+          const int cp = c + PF_A;
+          if (cp < nchunks) prefetch_l2(aimg + (size_t)cp * A_IMG2 + rank * APART, APART);
+          else if (un < g.units && cp - nchunks < nchunks)
+            prefetch_l2(im.a + (size_t)un * unit_img + (size_t)(cp - nchunks) * A_IMG2 + rank * APART, APART);
         }
       }
     }
