@@ -316,7 +316,8 @@ def run_gpu(args):
 
     def obs():
         P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
-                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"])
+                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"],
+                           prec=obc_prec)
 
     def step():
         obc()

@@ -182,7 +182,10 @@ negf_status negf_rgf_lesser(negf_ctx* ctx, const negf_system* sys, negf_precisio
                             void* GL_diag, void* GL_low,
                             int32_t* status, negf_stream stream);
 
-/* Observables, FP64 (Sec. III: DOS, spectral current, current conservation):
+/* Observables (Sec. III: DOS, spectral current, current conservation), traces and sums
+ * in FP64.  prec: the two block products of T (Gamma_L G_00 and G_00 Gamma_L) run in FP64
+ * with NEGF_FP64 and NEGF_MIXED_TF32, on the digit-sliced tensor-core path (FP64-class,
+ * 16 <= b <= 512) with NEGF_MIXED; any other value is NEGF_ERR_ARG.
  *   T[e]      = Tr[Gamma_L i(G_00 - G_00^H)] - Tr[Gamma_L G_00 Gamma_L G_00^H]     (needs GR_diag)
  *   dos[e]    = -(1/pi) Im Tr[G^R S] over the BT pattern                          (needs GR_diag,
  *               and GR_up, GR_low when S_up != NULL)
@@ -190,7 +193,7 @@ negf_status negf_rgf_lesser(negf_ctx* ctx, const negf_system* sys, negf_precisio
  *   density[k] = sum_e w[e] Re(-i (G^< S)_kk) / (2 pi)                          (needs GL_diag,
  *               GL_low when S_up != NULL; e_weight device [sum ne])
  * Each output may be NULL (skipped).  T: [sum ne], dos: [sum ne]. */
-negf_status negf_observables(negf_ctx* ctx, const negf_system* sys,
+negf_status negf_observables(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
                              const void* sigma_L, const double* e_weight,
                              const void* GR_diag, const void* GR_up, const void* GR_low,
                              const void* GL_diag, const void* GL_low,

@@ -1371,7 +1371,8 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
   return NEGF_OK;
 }
 
-negf_status negf_observables(negf_ctx* c, const negf_system* sys, const void* sigma_L, const double* e_weight,
+negf_status negf_observables(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* sigma_L,
+                             const double* e_weight,
                              const void* GR_diag, const void* GR_up, const void* GR_low, const void* GL_diag,
                              const void* GL_low, double* T, double* dos, double* current, double* density,
                              negf_stream stream) {
@@ -1388,6 +1389,8 @@ negf_status negf_observables(negf_ctx* c, const negf_system* sys, const void* si
   if (current && !GL_low) return fail(ctx, NEGF_ERR_ARG, "current needs GL_low");
   if (density && (!GL_diag || !e_weight || (overlap && !GL_low)))
     return fail(ctx, NEGF_ERR_ARG, "density needs GL_diag, e_weight (and GL_low when S_up is given)");
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
   CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Engine eng{ctx, s, 0, nullptr};
@@ -1400,8 +1403,14 @@ negf_status negf_observables(negf_ctx* c, const negf_system* sys, const void* si
     const int b = dv.b, nb = dv.nb;
     const long long bb = (long long)b * b;
     const long long N = (long long)nb * b;
-    const size_t per = std::max<size_t>(sizeof(zc) * (size_t)bb * 4, sizeof(double) * (size_t)N);
-    int chunk = (int)std::min<size_t>(ctx->ws_bytes / per, (size_t)65535);
+    // T's products on the sliced tensor-core path (FP64-class) when asked for and supported;
+    // their scales and digit images follow Gamma, K1 and K2 in the workspace
+    const int sl = (T && prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
+    eng.mixed = sl;
+    const size_t per = std::max<size_t>(sizeof(zc) * (size_t)bb * 4 + (sl ? ozt_scratch_bytes(b, 1) : 0),
+                                        sizeof(double) * (size_t)N);
+    const size_t avail = ctx->ws_bytes > 4096 ? ctx->ws_bytes - 4096 : 0;
+    int chunk = (int)std::min<size_t>(avail / per, (size_t)65535);
     if (chunk < 1) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one energy");
     chunk = std::min(chunk, ne);
     for (int e0 = 0; e0 < ne; e0 += chunk) {
@@ -1409,6 +1418,7 @@ negf_status negf_observables(negf_ctx* c, const negf_system* sys, const void* si
       if (T) {
         zc* p = (zc*)ctx->ws;
         BMat Gam{p, bb}, K1{p + (long long)U * bb, bb}, K2{p + 2LL * U * bb, bb};
+        eng.ozt_scratch = sl ? (void*)(((uintptr_t)(p + 3LL * U * bb) + 1023) & ~(uintptr_t)1023) : nullptr;
         BMat Sg{(zc*)sigma_L + o[3] + (long long)e0 * bb, bb};
         BMat G00{(zc*)GR_diag + o[4] + (long long)e0 * nb * bb, (long long)nb * bb};
         dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), U);

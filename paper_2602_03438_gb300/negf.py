@@ -90,7 +90,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                       vp, vp, vp, vp, vp]
     lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                     vp, vp, vp, vp, vp, vp, vp]
-    lib.negf_observables.argtypes = [vp, C.POINTER(_System), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_observables.argtypes = [vp, C.POINTER(_System), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_block_gemm.argtypes = [vp, C.c_int, i32, i32, i32, i32, vp, vp, C.c_int64, vp, C.c_int64, vp, vp,
                                     C.c_int64, vp, C.c_int64, vp]
     lib.negf_block_inverse.argtypes = [vp, C.c_int, i32, i32, vp, vp, vp, vp]
@@ -308,9 +308,9 @@ def negf_rgf_lesser(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R,
 
 def negf_observables(ctx: Context, sys: System, sigma_L=None, e_weight=None, GR_diag=None, GR_up=None,
                      GR_low=None, GL_diag=None, GL_low=None, T=None, dos=None, current=None, density=None,
-                     stream=None):
+                     stream=None, prec: int = FP64):
     s = sys.c()
-    ctx.check(ctx.lib.negf_observables(ctx.h, C.byref(s), _ptr(sigma_L), _ptr(e_weight), _ptr(GR_diag),
+    ctx.check(ctx.lib.negf_observables(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(e_weight), _ptr(GR_diag),
                                        _ptr(GR_up), _ptr(GR_low), _ptr(GL_diag), _ptr(GL_low), _ptr(T), _ptr(dos),
                                        _ptr(current), _ptr(density), _stream(stream)))
 

@@ -62,7 +62,7 @@ def run_gpu(P, ctx, devs, prec, lesser=True, obc=True, sigma=None, scat=True, ob
     if obs:
         P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
                            out.get("GL_diag"), out.get("GL_low"), out["T"], out["dos"], out.get("current"),
-                           out.get("density"))
+                           out.get("density"), prec=prec)
     assert ctx.sync() == 0
     L = sys_.layout()
     res = []

@@ -44,7 +44,8 @@ def test_config2_full_launch_sampled_energies(P):
         P.negf_rgf_lesser(ctx, sys_, P.MIXED, out["sigma_L"], out["sigma_R"], fL, fR, None, out["GR_diag"],
                           out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
         P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
-                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"])
+                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"],
+                           prec=P.MIXED)
         assert ctx.sync() == 0
         assert int((out["obc_status"] != 0).sum()) == 0
         assert int((out["status"] != 0).sum()) == 0

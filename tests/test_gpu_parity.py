@@ -249,3 +249,33 @@ def test_obc_mixed_products_match_oracle(P, ctx, nb, b):
             assert np.linalg.norm(rmx[k][e] - sref) <= TOL_FP64 * np.linalg.norm(sref), (e, k)
         # the same stopping rule: decimation steps agree with the FP64 run's
         assert np.abs(rmx["iters"][e] - r64["iters"][e]).max() <= 1
+
+
+# --- observables with T's products on the sliced path --------------------------------------
+
+@pytest.mark.parametrize("nb,b", [(3, 24), (2, 128), (2, 200)])
+def test_observables_mixed_products_match_fp64(P, ctx, nb, b):
+    """T's two block products (Gamma_L G_00, G_00 Gamma_L) on the sliced tensor-core path
+    against FP64 products on the same G^R and Sigma: T within 1e-10 of max |T|; DOS,
+    current and density use no products and are identical."""
+    dev = strong_leads(W.banded_device(nb, b, 4, seed=300 + b, overlap=True), seed=b)
+    sys_ = P.upload(dev)
+    out = P.allocate_outputs(sys_)
+    fL = torch.from_numpy(dev.f_L()).cuda()
+    fR = torch.from_numpy(dev.f_R()).cuda()
+    w = torch.from_numpy(dev.weights()).cuda()
+    P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"])
+    P.negf_rgf_lesser(ctx, sys_, P.FP64, out["sigma_L"], out["sigma_R"], fL, fR, None, out["GR_diag"],
+                      out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
+    res = {}
+    for prec in (P.FP64, P.MIXED):
+        got = {k: torch.zeros_like(out[k]) for k in ("T", "dos", "current", "density")}
+        P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
+                           out["GL_diag"], out["GL_low"], got["T"], got["dos"], got["current"], got["density"],
+                           prec=prec)
+        assert ctx.sync() == 0
+        res[prec] = {k: v.cpu().numpy() for k, v in got.items()}
+    t64, tm = res[P.FP64]["T"], res[P.MIXED]["T"]
+    assert np.abs(tm - t64).max() <= 1e-10 * max(np.abs(t64).max(), 1e-6)
+    for k in ("dos", "current", "density"):
+        assert np.array_equal(res[P.FP64][k], res[P.MIXED][k]), k
