@@ -920,6 +920,7 @@ __global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* G
       for (int r = threadIdx.x; r < b; r += blockDim.x) acc += g[(long long)r * b + r].y;
     } else {
       const zc* S = dv.Sd + i * bb;
+#pragma unroll 4
       for (long long k = threadIdx.x; k < bb; k += blockDim.x) {   // sum_pq G_pq S_qp
         const int p = (int)(k / b), q = (int)(k - (long long)p * b);
         const zc v = zmul(g[k], S[(long long)q * b + p]);
@@ -932,6 +933,7 @@ __global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* G
       const zc* gu = GRu + ((long long)e * (nb - 1) + i) * bb;
       const zc* gl = GRl + ((long long)e * (nb - 1) + i) * bb;
       const zc* Su = dv.Su + i * bb;
+#pragma unroll 4
       for (long long k = threadIdx.x; k < bb; k += blockDim.x) {
         const int p = (int)(k / b), q = (int)(k - (long long)p * b);
         // G_{i,i+1}[p][q] S_{i+1,i}[q][p] with S_{i+1,i} = S_up^H: S_{i+1,i}[q][p] = conj(Su[p][q])
@@ -956,11 +958,15 @@ __global__ void current_kernel(DevView dv, const zc* GLl, int e0, double* J) {
   const zc* H = dv.Hu + i * bb;
   const zc* S = dv.Su ? dv.Su + i * bb : nullptr;
   double acc = 0.0;
+  // sum_pq A[p][q] G[q][p] with k running along G (coalesced reads of the per-energy block;
+  // A = H - z S is shared by all energies and read transposed from L2)
+#pragma unroll 4
   for (long long k = threadIdx.x; k < bb; k += blockDim.x) {
-    const int p = (int)(k / b), q = (int)(k - (long long)p * b);
-    zc x = H[k];
-    if (S) x = zsub(x, zmul(z, S[k]));
-    acc += zmul(x, g[(long long)q * b + p]).x;
+    const int q = (int)(k / b), p = (int)(k - (long long)q * b);
+    const long long t = (long long)p * b + q;
+    zc x = H[t];
+    if (S) x = zsub(x, zmul(z, S[t]));
+    acc += zmul(x, g[k]).x;
   }
   __shared__ double red[32];
   const double t = block_sum<256>(acc, red);
