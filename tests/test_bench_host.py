@@ -87,3 +87,26 @@ def test_roofline_sliced_gemm_counts_tensor_work():
     useful = 8 * 128 ** 3 * 100.0 / 2e-3 / 1e12
     assert abs(r["useful_tflops"] - useful) < 1e-9
     assert abs(r["achieved"] - 36 * useful) < 1e-9 and r["peak"] == 1650.0
+
+
+def test_traffic_record_matches_the_kernel_source(tmp_path, monkeypatch):
+    """The committed per-product DRAM traffic is reported only while the kernel source
+    it was captured from is unchanged (its hash recorded beside the figure)."""
+    import hashlib
+    import json
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "roofline_traffic.json")))["gemm_oz"]
+    src = os.path.join(bench.ROOT, rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    assert h == rec["source_sha256_16"]
+    assert bench.traffic_for("gemm_oz") == rec["bytes_per_launch_full"]
+    # at least the algorithmic bytes of one product (A, B read and D written once)
+    assert rec["bytes_per_launch_full"] >= 3 * 1024 * 128 * 128 * 16
+    # a changed source makes the figure stale: null
+    fake = tmp_path / "profiles"
+    fake.mkdir()
+    (tmp_path / "k.cu").write_text("changed")
+    (fake / "roofline_traffic.json").write_text(json.dumps(
+        {"gemm_oz": {"source": "k.cu", "source_sha256_16": h, "bytes_per_launch_full": 1}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("gemm_oz") is None
+    assert bench.traffic_for("inv_f32") is None
