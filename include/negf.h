@@ -239,9 +239,12 @@ negf_status negf_block_inverse(negf_ctx* ctx, negf_precision prec, int32_t n, in
  * NEGF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  Calls with 2 n units x 4 bytes above that size are rejected with
  * NEGF_ERR_ARG and a message from negf_last_error(NULL); split the batch.  Other n
- * use FP64 FMA and no scratch.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.  All calls share the array and it
+ * use FP64 FMA and no scratch.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress: host-side, allocates nothing), so the call
+ * stays valid across cudaDeviceReset, after which the array is loaded afresh (its old
+ * contents are gone, which this call never relies on); the first call on a device may
+ * load the library's device code there, so make it before any stream capture.  The
+ * kernels' function attributes are set once per device.  All calls share the array and it
  * keeps the last call's contents (every scale a call reads is written by that same
  * call first, so nothing needs clearing); calls whose kernels overlap on the GPU
  * (other streams) race on it -- serialize them.  `status` (device int32 or NULL)

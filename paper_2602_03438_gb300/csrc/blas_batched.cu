@@ -2,9 +2,30 @@
 // inversion (FP64 or FP32 arithmetic).  These are the building blocks of the
 // RGF recursions (every step is a product or an inverse of b x b blocks,
 // batched over independent energy points, Sec. II of the paper).
+#include <atomic>
+#include <mutex>
+
 #include "negf_internal.cuh"
 
 namespace negf {
+
+namespace {
+std::mutex g_init_mutex;
+std::atomic<bool> g_init_done[kMaxDevices][INIT_NSLOT];
+}  // namespace
+
+cudaError_t once_per_device(int slot, const std::function<cudaError_t(int device)>& init) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || slot < 0 || slot >= INIT_NSLOT) return cudaErrorInvalidValue;
+  if (g_init_done[dev][slot].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(g_init_mutex);
+  if (g_init_done[dev][slot].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = init(dev);
+  if (e == cudaSuccess) g_init_done[dev][slot].store(true, std::memory_order_release);
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 complex GEMM: D = alpha op(A) op(B) + beta C, one grid z-slice per unit.

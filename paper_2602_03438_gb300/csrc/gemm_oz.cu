@@ -150,14 +150,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(IDESC), "r"(acc)
       : "memory");
 }
-// completion of this thread's MMAs arrives on the same barrier offset in every member of ctaMask
-__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -327,23 +319,26 @@ __global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb, int first) {
 // CL CTAs of a cluster are the CL column tiles of one 128-row tile (grid x is padded to a
 // multiple of CL): each digitizes TM/CL of the A rows into every member's shared memory
 //
-// Warp roles: warps 0..7 produce digits (and run the epilogue), warp 8 issues the MMAs.
-// Handshakes are mbarriers only: full[s] collects one arrival per producer warp of every
-// member (their stores into this member's stage s are done), empty[s] one multicast
-// commit per member (its MMAs reading stage s are done; they read A rows that this
-// member wrote).
+// Warp roles: warps 0..7 produce digits (and run the epilogue), warp 8 issues the MMAs,
+// warp 9 releases stages.  Handshakes are mbarriers only: full[s] collects one arrival
+// per producer warp of every member (their stores into this member's stage s are
+// done); mdone[s] the commit of this member's MMAs reading stage s; empty[s] one
+// arrival per member, sent by that member's release warp once its mdone[s] phase has
+// completed (its MMAs read A rows that this member wrote, so a producer may overwrite
+// stage s only when every member's MMAs are done with it).
 template <int CL>
-__global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const int* ea, const int* eb, int* err,
+__global__ void __launch_bounds__(NT + 64, 1) zgemm_oz_kernel(GemmArgs g, const int* ea, const int* eb, int* err,
                                                              int unit_alpha_beta) {
   const int u = blockIdx.z;
   if (g.active && !g.active[u]) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE);   // full[2], empty[2], done
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGE);   // full[2], empty[2], done, mdone[2]
   uint64_t* full = bars;
   uint64_t* empty = bars + 2;
   uint64_t* done = bars + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE + 48);
+  uint64_t* mdone = bars + 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE + 56);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -360,6 +355,8 @@ __global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const 
     mbar_init(&empty[0], CL);
     mbar_init(&empty[1], CL);
     mbar_init(done, 1);
+    mbar_init(&mdone[0], 1);
+    mbar_init(&mdone[1], 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -435,9 +432,20 @@ __global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const 
             }
           }
         }
-        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+        mma_commit(&mdone[s]);
       }
       mma_commit(done);
+    }
+  } else if (warp == 9) {
+    // ---------------- release warp: once this member's MMAs of chunk c are done, one
+    // arrival on empty[c & 1] of every member (only chunks whose stage is refilled)
+    if (lane == 0) {
+      for (int c = 0; c + 2 < nchunks; ++c) {
+        const int s = c & 1;
+        if (!mbar_wait(&mdone[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) mbar_arrive_remote(mapa_shared(smem_u32(&empty[s]), (uint32_t)r));
+      }
     }
   } else {
   // ---------------- producer warps
@@ -586,9 +594,10 @@ __global__ void __launch_bounds__(NT + 32, 1) zgemm_oz_kernel(GemmArgs g, const 
 // Digitize-once variant.  oz_digitize_a writes the A operand's digits as pre-swizzled
 // shared-memory images in global memory ([unit][row tile][chunk][digit] planes, exactly
 // the stage layout of the MMA) with the row scale exponents; zgemm_ozt_kernel streams
-// them with bulk copies (each member copies 1/CL of a chunk's image and multicasts it
-// to the whole cluster), digitizes its own 32 B columns in four producer warps, and
-// issues the MMAs from one thread.
+// them with bulk copies (every CTA copies each chunk's whole image into its own shared
+// memory; the column tiles of a row tile run as one cluster, so that they are resident
+// on the same die together and their copies of the shared image hit the L2),
+// digitizes its own 32 B columns in producer warps, and issues the MMAs from one thread.
 // ===========================================================================
 constexpr uint32_t A_IMG = NS * A_SLICE;   // one chunk of one 128-row A tile (64 KB)
 
@@ -686,15 +695,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-// bulk copy global -> the same shared offset of every member in `mask`, counted on each
-// member's barrier at the same offset
-__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                                   uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
+// bulk copy of `bytes` (a multiple of 16) from a 16-byte aligned global address into this
+// CTA's shared memory at `dst` (16-byte aligned), counted on this CTA's barrier `bar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 constexpr int NPW = 8;                 // B-digit producer / epilogue warps
@@ -719,11 +725,12 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   const int nchunks = im.c_count;   // chunks c_begin .. c_begin + c_count - 1 of K
 
   if (tid == 0) {
-    // full[s]: the A copy producer (expect_tx) and the NPW B producer warps
+    // full[s]: the A copy producer (expect_tx) and the NPW B producer warps; empty[s]:
+    // this CTA's MMA commit
     mbar_init(&full[0], NPW + 1);
     mbar_init(&full[1], NPW + 1);
-    mbar_init(&empty[0], CL);
-    mbar_init(&empty[1], CL);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
     mbar_init(done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -738,23 +745,19 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t rank = cluster_ctarank();
   const uint32_t lbase = smem_u32(base);
   const int* eB = im.eb + (size_t)u * n;
-  cluster_sync();   // every member's barriers are initialized before copies arrive
 
   if (warp == NPW) {
-    // ---------------- A: this member's 1/CL of the digit image, multicast to every member
+    // ---------------- A: each chunk's whole digit image, into this CTA's stage
     if (lane == 0) {
       const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * im.nchunks) * A_IMG;
-      constexpr uint32_t APART = A_IMG / CL;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
-        if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+        if (c >= 2 && !mbar_wait(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
         const uint32_t st_off = (uint32_t)(s * STAGE);
         mbar_expect_tx(&full[s], A_IMG);
-        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)(im.c_begin + c) * A_IMG + rank * APART,
-                           APART, &full[s], (uint16_t)((1u << CL) - 1u));
+        bulk_g2s(lbase + st_off, aimg + (size_t)(im.c_begin + c) * A_IMG, A_IMG, &full[s]);
       }
     }
   } else if (warp == NPW + 1) {
@@ -762,7 +765,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
     if (lane == 0) {
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
-        if (!mbar_wait_cluster(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+        if (!mbar_wait(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st_off = (uint32_t)(s * STAGE);
         const uint64_t da = sdesc64(lbase + st_off), db = sdesc64(lbase + st_off + A_IMG);
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
         for (int ks = 0; ks < 2; ++ks)   // two 16-element K steps per 64-byte row
           slice_mmas<NR>(tmem, da + (uint64_t)((ks * 32) >> 4), db + (uint64_t)((ks * 32) >> 4), A_SLICE >> 4,
                          B_SLICE >> 4, c == 0 && ks == 0);
-        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+        mma_commit(&empty[s]);
       }
       mma_commit(done);
     }
@@ -794,7 +797,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
     const uint32_t o1 = sw64(bn, bk), o2 = sw64(bn, KC + bk), o3 = sw64(TNC + bn, bk), o4 = sw64(TNC + bn, KC + bk);
     for (int c = 0; c < nchunks; ++c) {
       const int s = c & 1;
-      if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+      if (c >= 2 && !mbar_wait(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
       zc cb[2];
       cb[0] = rb[0];
       cb[1] = rb[1];
@@ -894,7 +897,6 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
-  cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
 
 // ===========================================================================
@@ -902,8 +904,9 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
 // K chunks of 8 complex (32-byte rows, 32-byte swizzle): 8 accumulator groups x 32
 // columns = 256 TMEM columns and two 40 KB stages per CTA, so that two CTAs share an
 // SM and one's epilogue (integer recombination, issue-bound) overlaps the other's
-// MMAs.  The column tiles of a row tile form a cluster that shares the A digit image
-// by multicast bulk copies.
+// MMAs.  Every CTA copies the A digit image of its row tile into its own shared memory;
+// the column tiles of a row tile run as one cluster (resident on one die together, so
+// that their copies of the same image hit the L2).
 // ===========================================================================
 constexpr int TNC2 = 16;                              // complex columns per tile
 constexpr int NR2 = 2 * TNC2;                         // real MMA columns (32)
@@ -1063,8 +1066,8 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
   if (tid == 0) {
     mbar_init(&full[0], 5);   // the A copy producer (expect_tx) and the four B producer warps
     mbar_init(&full[1], 5);
-    mbar_init(&empty[0], CL);
-    mbar_init(&empty[1], CL);
+    mbar_init(&empty[0], 1);  // this CTA's MMA commit
+    mbar_init(&empty[1], 1);
     mbar_init(done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1079,23 +1082,19 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t rank = cluster_ctarank();
   const uint32_t lbase = smem_u32(base);
   const int* eB = im.eb + (size_t)u * n;
-  cluster_sync();   // every member's barriers are initialized before copies arrive
 
   if (warp == 4) {
-    // ---------------- A: this member's 1/CL of the digit image, multicast to every member
+    // ---------------- A: each chunk's whole digit image, into this CTA's stage
     if (lane == 0) {
       const unsigned char* aimg = im.a + ((size_t)(u * im.tiles_m + tm) * nchunks) * A_IMG2;
-      constexpr uint32_t APART = A_IMG2 / CL;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
-        if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+        if (c >= 2 && !mbar_wait(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
         const uint32_t st_off = (uint32_t)(s * STAGE2);
         mbar_expect_tx(&full[s], A_IMG2);
-        bulk_g2s_multicast(lbase + st_off + rank * APART, aimg + (size_t)c * A_IMG2 + rank * APART, APART,
-                           &full[s], (uint16_t)((1u << CL) - 1u));
+        bulk_g2s(lbase + st_off, aimg + (size_t)c * A_IMG2, A_IMG2, &full[s]);
       }
     }
   } else if (warp == 5) {
@@ -1103,12 +1102,12 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
     if (lane == 0) {
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
-        if (!mbar_wait_cluster(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+        if (!mbar_wait(&full[s], (uint32_t)((c >> 1) & 1))) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st_off = (uint32_t)(s * STAGE2);
         const uint64_t da = sdesc32(lbase + st_off), db = sdesc32(lbase + st_off + A_IMG2);
         slice_mmas<NR2>(tmem, da, db, A_SLICE2 >> 4, B_SLICE2 >> 4, c == 0);
-        mma_commit_multicast(&empty[s], (uint16_t)((1u << CL) - 1u));
+        mma_commit(&empty[s]);
       }
       mma_commit(done);
     }
@@ -1129,7 +1128,7 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
                    o4 = sw32(TNC2 + bn, KC2 + bk);
     for (int c = 0; c < nchunks; ++c) {
       const int s = c & 1;
-      if (c >= 2 && !mbar_wait_cluster(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+      if (c >= 2 && !mbar_wait(&empty[s], (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
       const zc cb = rb;
       if (c + 1 < nchunks) rb = loadb(c + 1);
       int dr[NS], di[NS];
@@ -1215,13 +1214,14 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
   }
-  cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
 
 // ===========================================================================
 // Persistent variant for 96 < n <= 128: the epilogue of tile t overlaps the MMAs of
-// tile t+1.  One CTA per SM, clusters of 4 (the column tiles of one unit) walk the
-// units in turn.  Full-width tiles (128 x 32 complex, N = 64 per MMA, 512 TMEM
+// tile t+1.  One CTA per SM; the 4 column tiles of a unit are 4 consecutive CTAs (one
+// cluster, resident on one die, each copying the unit's whole A image into its own
+// shared memory, so that all but the first read of an image hit the L2), and these
+// groups walk the units in turn.  Full-width tiles (128 x 32 complex, N = 64 per MMA, 512 TMEM
 // columns), K chunks of 8 complex (32-byte rows, 32-byte swizzle, two 48 KB stages;
 // the A digit images are those of the half-width kernel).  After a tile's MMAs the
 // epilogue warps drain TMEM into a shared-memory buffer of exact int32 group pairs
@@ -1254,15 +1254,15 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = g.n;
   const int nchunks = (n + KCP - 1) / KCP;
-  const uint32_t rank = cluster_ctarank();
+  const uint32_t rank = blockIdx.x % CL;   // column tile
   const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int n0 = (int)rank * TNC;
 
   if (tid == 0) {
     mbar_init(&full[0], 5);   // the A copy (expect_tx) and the four B warps of the stage's group
     mbar_init(&full[1], 5);
-    mbar_init(&empty[0], CL);
-    mbar_init(&empty[1], CL);
+    mbar_init(&empty[0], 1);  // this CTA's MMA commit
+    mbar_init(&empty[1], 1);
     mbar_init(done, 1);
     mbar_init(tfree, 8);
     s_fail = 0;
@@ -1279,14 +1279,13 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t lbase = smem_u32(base);
-  cluster_sync();   // every member's barriers are initialized before copies arrive
   auto skip = [&](int u) { return g.active && !g.active[u]; };
 
   if (warp == 16) {
-    // ---------------- A: this member's quarter of each chunk's digit image, multicast
-    // (this member's part of the image PF_A chunks ahead, of this unit or the next, is
-    // prefetched into L2 when a chunk is copied, so that the copies, which wait for a free
-    // stage, read L2 rather than DRAM)
+    // ---------------- A: each chunk's whole digit image, into this CTA's stage (this
+    // column tile's quarter of the image PF_A chunks ahead, of this unit or the next, is
+    // prefetched into L2 when a chunk is copied, so that the four tiles' copies, which
+    // wait for a free stage, read L2 rather than DRAM)
     if (lane == 0) {
       constexpr uint32_t APART = A_IMG2 / CL;
       constexpr int PF_A = 4;
@@ -1304,10 +1303,9 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
         }
         for (int c = 0; c < nchunks; ++c, ++cg) {
           const int st = cg & 1;
-          if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
+          if (cg >= 2 && !mbar_wait(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
           mbar_expect_tx(&full[st], A_IMG2);
-          bulk_g2s_multicast(lbase + st * STAGE_P + rank * APART, aimg + (size_t)c * A_IMG2 + rank * APART, APART,
-                             &full[st], (uint16_t)((1u << CL) - 1u));
+          bulk_g2s(lbase + st * STAGE_P, aimg + (size_t)c * A_IMG2, A_IMG2, &full[st]);
           const int cp = c + PF_A;
           if (cp < nchunks) prefetch_l2(aimg + (size_t)cp * A_IMG2 + rank * APART, APART);
           else if (un < g.units && cp - nchunks < nchunks)
@@ -1325,11 +1323,11 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         for (int c = 0; c < nchunks; ++c, ++cg) {
           const int st = cg & 1;
-          if (!mbar_wait_cluster(&full[st], (cg >> 1) & 1)) { s_fail = 1; break; }
+          if (!mbar_wait(&full[st], (cg >> 1) & 1)) { s_fail = 1; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t da = sdesc32(lbase + st * STAGE_P), db = sdesc32(lbase + st * STAGE_P + A_IMG2);
           slice_mmas<NR>(tmem, da, db, A_SLICE2 >> 4, B_SLICE_P >> 4, c == 0);
-          mma_commit_multicast(&empty[st], (uint16_t)((1u << CL) - 1u));
+          mma_commit(&empty[st]);
         }
         if (s_fail) break;
         mma_commit(done);
@@ -1407,7 +1405,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
         }
       }
       const int st = cg & 1;
-      if (cg >= 2 && !mbar_wait_cluster(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
+      if (cg >= 2 && !mbar_wait(&empty[st], ((cg - 2) >> 1) & 1)) { s_fail = 1; break; }
       unsigned char* Bsl = base + st * STAGE_P + A_IMG2;
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
@@ -1508,7 +1506,6 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
-  cluster_sync();   // no member leaves while copies into its shared memory may be pending
 }
 
 }  // namespace
@@ -1524,20 +1521,19 @@ cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s)
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
   // cluster size: a tuning parameter (NEGF_OZ_CLUSTER = 2 or 4, default kCluster)
-  static int CL = 0;
-  if (CL == 0) {
-    const char* env = getenv("NEGF_OZ_CLUSTER");
-    CL = (env && atoi(env) == 2) ? 2 : kCluster;
-    cudaError_t e = cudaFuncSetAttribute(zgemm_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(zgemm_oz_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) { CL = 0; return e; }
-  }
+  const char* env = getenv("NEGF_OZ_CLUSTER");
+  const int CL = (env && atoi(env) == 2) ? 2 : kCluster;
+  cudaError_t e = once_per_device(INIT_OZ, [](int) {
+    cudaError_t r = cudaFuncSetAttribute(zgemm_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(zgemm_oz_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   int* ea = (int*)scratch;
   int* eb = ea + (size_t)g.n * g.units;
   oz_scale_kernel<<<dim3(2, g.units), 256, 0, s>>>(g, ea, eb, 0);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
                        (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
@@ -1545,7 +1541,7 @@ cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s)
   const int tiles_n = (g.n + TNC - 1) / TNC;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((tiles_n + CL - 1) / CL * CL, (g.n + TM - 1) / TM, g.units);
-  cfg.blockDim = dim3(NT + 32, 1, 1);
+  cfg.blockDim = dim3(NT + 64, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -1575,16 +1571,13 @@ size_t ozt_scratch_bytes(int n, int units) {
 
 // half-width tiles, two CTAs per SM; cluster = the column tiles sharing one A image
 static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_ozs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(zgemm_ozs_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(zgemm_ozs_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = once_per_device(INIT_OZS, [](int) {
+    cudaError_t r = cudaFuncSetAttribute(zgemm_ozs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(zgemm_ozs_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(zgemm_ozs_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   const int n = g.n;
   const int tn = (n + TNC2 - 1) / TNC2;
   const int CL = (tn % 8 == 0) ? 8 : (tn % 4 == 0) ? 4 : 2;
@@ -1601,7 +1594,7 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.a = p;
   // A digit images and op(B)'s column scales in one launch (n <= 96 here)
   oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
                        (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
@@ -1626,8 +1619,9 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
 }
 
 // persistent full-width tiles with the epilogue overlapping the next tile (96 < n <= 128)
+static int g_ozp_clusters[kMaxDevices];   // co-resident clusters of the persistent kernel, per device
+
 static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
-  static int max_clusters = 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1639,17 +1633,24 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (max_clusters == 0) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = once_per_device(INIT_OZP, [&cfg](int d) {
+    cudaError_t r = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_P);
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(CL_P, 1, 1);
+    if (r != cudaSuccess) return r;
+    cudaLaunchConfig_t q = cfg;
+    q.gridDim = dim3(CL_P, 1, 1);
     int ncl = 0;
-    e = cudaOccupancyMaxActiveClusters(&ncl, zgemm_ozp_kernel<CL_P>, &cfg);
-    if (e != cudaSuccess) return e;
+    r = cudaOccupancyMaxActiveClusters(&ncl, zgemm_ozp_kernel<CL_P>, &q);
+    if (r != cudaSuccess) return r;
     if (ncl < 1) return cudaErrorInvalidConfiguration;
-    max_clusters = ncl;
-  }
+    g_ozp_clusters[d] = ncl;
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  const int max_clusters = g_ozp_clusters[dev];
   const int n = g.n;
   OzImages im;
   im.nchunks = (n + KC2 - 1) / KC2;
@@ -1664,7 +1665,7 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.a = p;
   // A digit images and op(B)'s column scales in one launch
   oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
                        (!g.C.p || (g.beta.y == 0.0 && (g.beta.x == 0.0 || g.beta.x == 1.0 || g.beta.x == -1.0))))
@@ -1694,13 +1695,10 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
   constexpr int CL = kCluster;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_ozt_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = once_per_device(INIT_OZT, [](int) {
+    return cudaFuncSetAttribute(zgemm_ozt_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (e != cudaSuccess) return e;
   const int n = g.n;
   OzImages im;
   im.nchunks = (n + KC - 1) / KC;
@@ -1712,7 +1710,7 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
   oz_digitize_a_kernel<<<dim3(im.tiles_m * (TM / 32), g.units), 256, 0, s>>>(g, im);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -276,12 +276,10 @@ bool tc_supported(int n) { return n >= 16; }
 
 cudaError_t zgemm_tc(const GemmArgs& g, int* err, cudaStream_t s) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = once_per_device(INIT_TC, [](int) {
+    return cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (e != cudaSuccess) return e;
   const int tiles = (g.n + TM - 1) / TM;
   dim3 grid(tiles, tiles, g.units);
   zgemm_tc_kernel<<<grid, NT, SMEM_BYTES, s>>>(g, err);

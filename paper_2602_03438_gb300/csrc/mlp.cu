@@ -502,11 +502,9 @@ negf_status gemm(Ctx* ctx, cudaStream_t s, const bf16* A, long long lda, const b
                  int K, const Epi& ep) {
   const Fail F{ctx};
   if (M % BM || N % BN || K % BK || K <= 0) return F(NEGF_ERR_ARG, "GEMM shape not a multiple of the tiles");
-  static bool attr_set = false;
-  if (!attr_set) {
-    MCU(cudaFuncSetAttribute(bf16_gemm_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM));
-    attr_set = true;
-  }
+  MCU(once_per_device(INIT_MLP, [](int) {
+    return cudaFuncSetAttribute(bf16_gemm_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  }));
   CUtensorMap ma, mb;
   negf_status st;
   if ((st = make_map(F, &ma, A, M, K, lda)) != NEGF_OK) return st;

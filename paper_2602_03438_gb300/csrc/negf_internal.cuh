@@ -4,12 +4,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
 #include "../../include/negf.h"
 
 namespace negf {
+
+// ---------------------------------------------------------------------------
+// one-time set-up per GPU: kernel function attributes (dynamic shared memory size,
+// occupancy queries) are properties of a device, so each device gets its own set-up,
+// and several host threads may arrive at once.  `init(device)` runs with that device
+// current, under a process-wide lock, at most once per (device, slot); a failed init
+// is not recorded, so the next call retries it.
+// ---------------------------------------------------------------------------
+enum InitSlot { INIT_OZ = 0, INIT_OZS, INIT_OZP, INIT_OZT, INIT_TC, INIT_MLP, INIT_NSLOT };
+constexpr int kMaxDevices = 64;
+cudaError_t once_per_device(int slot, const std::function<cudaError_t(int device)>& init);
 
 typedef double2 zc;   // complex128, interleaved (re, im)
 typedef float2 cc;    // complex64

@@ -11,8 +11,10 @@
 // product (4 bytes x 2 n per unit).  They live in the file-scope device array
 // below, of kNoAllocScratchBytes; every GPU that loads the library holds it until
 // the process exits.  Host code cannot use the array's name as a device address,
-// so the device address is looked up once per device with cudaGetSymbolAddress.
-#include <mutex>
+// so every call looks the address up with cudaGetSymbolAddress, with the caller's
+// device current: a host-side lookup that allocates nothing, and that stays right
+// when the device's context is destroyed and created again (cudaDeviceReset), which
+// may load the array at another address.
 #include <string>
 
 #include "negf_internal.cuh"
@@ -23,23 +25,6 @@ constexpr size_t kNoAllocScratchBytes = NEGF_NOALLOC_SCRATCH_BYTES;
 static_assert(kNoAllocScratchBytes % 256 == 0, "scratch size must keep 256-byte alignment");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_lookup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// device address of the scratch array on the current device (looked up on first use)
-cudaError_t scratch_address(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_lookup_mutex);
-  if (!g_scratch_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[device] = p;
-  }
-  *out = g_scratch_ptr[device];
-  return cudaSuccess;
-}
 
 }  // namespace
 
@@ -75,7 +60,7 @@ extern "C" negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t
   if (units == 0) return NEGF_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess || dev < 0 || dev >= negf::kMaxDevices) {
     negf_set_error_message("negf_block_gemm_noalloc: no usable current device");
     return NEGF_ERR_CUDA;
   }
@@ -94,7 +79,7 @@ extern "C" negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   if (sliced) {
     void* scratch = nullptr;
-    e = scratch_address(dev, &scratch);
+    e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
     if (e == cudaSuccess) e = zgemm_oz(g, scratch, (int*)status, s);
   } else {
     e = zgemm_f64(g, s);

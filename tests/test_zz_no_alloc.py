@@ -82,3 +82,26 @@ def test_noalloc_rejects_batches_beyond_its_scratch(P):
         P.negf.negf_block_gemm_noalloc(A, A[0], D)
     assert ei.value.code == P.negf.NEGF_ERR_ARG
     assert "static array" in str(ei.value)
+
+
+def test_noalloc_on_a_second_device(P):
+    """The kernels' shared-memory attributes are set per device: the first call on a
+    second GPU must work like the first (skipped when one GPU is visible)."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one CUDA device visible")
+    n, U = 128, 4
+    rng = np.random.default_rng(77)
+    A, B = _rand(rng, (U, n, n)), _rand(rng, (U, n, n))
+    exact = A @ B
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            tA = torch.from_numpy(A).to(f"cuda:{dev}")
+            tB = torch.from_numpy(B).to(f"cuda:{dev}")
+            D = torch.empty_like(tA)
+            status = torch.zeros(1, dtype=torch.int32, device=f"cuda:{dev}")
+            P.negf.negf_block_gemm_noalloc(tA, tB, D, status=status, stream=torch.cuda.current_stream(dev))
+            torch.cuda.synchronize(dev)
+            assert int(status.item()) == 0
+            got = D.cpu().numpy()
+            size = np.linalg.norm(A, axis=2)[:, :, None] * np.linalg.norm(B, axis=1)[:, None, :]
+            assert (np.abs(got - exact) / size).max() <= TOL, dev
