@@ -7,7 +7,8 @@ paper's statement of the problem:
 
   * Eq. (1):  C^R = (A - B^R)^{-1}.  For electrons
               G^R(E) = (z S - H - Sigma^R_OBC - Sigma^R_scat)^{-1}, z = E + i eta.
-  * Eq. (2):  (C^R)^{-1} C^< (C^R)^{-H} = B^<,  i.e.  G^< = G^R Sigma^< G^A.
+  * Eq. (2):  (C^R)^{-1} C^< (C^R)^{-H} = B^<,  i.e.  G^< = G^R Sigma^< G^A;
+              the same relation with B^> gives G^> = G^R Sigma^> G^A.
   * Sec. II:  A and B are block-tridiagonal; only the entries of C on that
               pattern (diagonal and first off-diagonal blocks) are wanted, and
               every energy is independent.
@@ -31,7 +32,8 @@ import numpy as np
 
 __all__ = [
     "dense_matrix", "dense_H_S", "lead_A_blocks", "sancho_rubio", "surface_residual",
-    "lead_self_energies", "lead_lesser", "gamma", "assemble_A", "assemble_sigma_lesser",
+    "lead_self_energies", "lead_lesser", "lead_greater", "scattering_greater", "gamma", "assemble_A",
+    "assemble_sigma_lesser", "assemble_sigma_greater",
     "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
     "interface_current", "density", "solve_energy", "retarded_check", "surface_newton_warm",
     "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf",
@@ -290,6 +292,23 @@ def lead_lesser(sigma, f):
     return 1j * f * gamma(sigma)
 
 
+def lead_greater(sigma, f):
+    """Lead greater self-energy Sigma^> = -i (1 - f) Gamma (holes injected by the lead)."""
+    return -1j * (1.0 - f) * gamma(sigma)
+
+
+def scattering_greater(sigR_scat_i, sigL_scat_i):
+    """Sigma^>_scat = Sigma^<_scat + Sigma^R_scat - Sigma^A_scat: the retarded
+    self-energy's anti-Hermitian part is Sigma^> - Sigma^< for any self-energy
+    of the Keldysh form."""
+    out = np.zeros_like(sigR_scat_i if sigR_scat_i is not None else sigL_scat_i, dtype=np.complex128)
+    if sigL_scat_i is not None:
+        out = out + sigL_scat_i
+    if sigR_scat_i is not None:
+        out = out + sigR_scat_i - _H(sigR_scat_i)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Eq. (1) and Eq. (2) by dense inversion
 # ---------------------------------------------------------------------------
@@ -321,13 +340,30 @@ def assemble_sigma_lesser(dev, sigma_L, sigma_R, fL, fR, sigL_scat=None):
     return SL
 
 
+def assemble_sigma_greater(dev, sigma_L, sigma_R, fL, fR, sigR_scat=None, sigL_scat=None):
+    """Dense block-diagonal Sigma^> = Sigma^>_scat - i (1 - f_L) Gamma_L (block 0)
+    - i (1 - f_R) Gamma_R (block nb-1), the B^> that gives C^> = C^R B^> C^A in the
+    same way as Eq. (2) gives C^<."""
+    b, nb = dev.b, dev.nb
+    N = nb * b
+    SG = np.zeros((N, N), dtype=np.complex128)
+    _blk(SG, 0, 0, b)[...] += lead_greater(sigma_L, fL)
+    _blk(SG, nb - 1, nb - 1, b)[...] += lead_greater(sigma_R, fR)
+    if sigR_scat is not None or sigL_scat is not None:
+        for i in range(nb):
+            _blk(SG, i, i, b)[...] += scattering_greater(None if sigR_scat is None else sigR_scat[i],
+                                                         None if sigL_scat is None else sigL_scat[i])
+    return SG
+
+
 def greens_dense(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_scat=None,
-                 keep_dense=False):
+                 keep_dense=False, greater=False):
     """Selected blocks of G^R (Eq. (1)) and, when occupations are given, of
-    G^< = G^R Sigma^< G^A (Eq. (2)), by inverting the full matrix.
+    G^< = G^R Sigma^< G^A (Eq. (2)), by inverting the full matrix; with
+    `greater`, also G^> = G^R Sigma^> G^A.
 
     Returns a dict with GR_diag [nb], GR_up [nb-1] (block (i,i+1)),
-    GR_low [nb-1] (block (i+1,i)), and GL_diag, GL_low likewise."""
+    GR_low [nb-1] (block (i+1,i)), GL_diag, GL_low likewise, and GG_diag, GG_low."""
     b, nb = dev.b, dev.nb
     A = assemble_A(dev, z, sigma_L, sigma_R, sigR_scat)
     G = np.linalg.inv(A)
@@ -348,6 +384,15 @@ def greens_dense(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sig
         if keep_dense:
             out["GL"] = GL
             out["SigmaL"] = SL
+        if greater:
+            SG = assemble_sigma_greater(dev, sigma_L, sigma_R, fL, fR, sigR_scat, sigL_scat)
+            GG = G @ SG @ _H(G)
+            out["GG_diag"] = np.stack([_blk(GG, i, i, b) for i in range(nb)])
+            out["GG_low"] = (np.stack([_blk(GG, i + 1, i, b) for i in range(nb - 1)])
+                             if nb > 1 else np.zeros((0, b, b), complex))
+            if keep_dense:
+                out["GG"] = GG
+                out["SigmaG"] = SG
     if keep_dense:
         out["G"] = G
         out["A"] = A
@@ -372,8 +417,31 @@ def _A_blocks(dev, z, sigma_L, sigma_R, sigR_scat=None):
     return Ad, Au, Al
 
 
-def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_scat=None):
-    """Selected blocks of G^R and G^< by the forward/backward block recursion.
+def _keldysh_sweep(g, GR_d, GR_u, Au, Al, Sig):
+    """Forward and backward sweeps of C^x = C^R Sigma^x C^A for one block-diagonal
+    Sigma^x (x = <, or >: the recursion is linear in Sigma^x).  Returns the diagonal
+    and lower blocks."""
+    nb = len(g)
+    gl = [None] * nb
+    gl[0] = g[0] @ Sig[0] @ _H(g[0])
+    for i in range(1, nb):
+        gl[i] = g[i] @ (Sig[i] + Al[i - 1] @ gl[i - 1] @ _H(Al[i - 1])) @ _H(g[i])
+    Gd = [None] * nb
+    Gl = [None] * (nb - 1)
+    Gd[nb - 1] = gl[nb - 1]
+    for i in range(nb - 2, -1, -1):
+        X = g[i] @ Au[i]
+        Z = Al[i] @ gl[i]
+        P = Gd[i + 1] @ _H(X)
+        W = GR_u[i] @ Z
+        Gd[i] = gl[i] + X @ P - W + _H(W)
+        Gl[i] = -GR_d[i + 1] @ Z - P
+    return Gd, Gl
+
+
+def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_scat=None, greater=False):
+    """Selected blocks of G^R and G^< (and, with `greater`, G^>) by the
+    forward/backward block recursion.
 
     Forward:  g_0 = A_00^{-1},  g_i = (A_ii - A_{i,i-1} g_{i-1} A_{i-1,i})^{-1};
               g^<_i = g_i (Sigma^<_ii + A_{i,i-1} g^<_{i-1} A_{i,i-1}^H) g_i^H.
@@ -382,7 +450,8 @@ def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_
               G_ii = g_i - G_{i,i+1} Y;
               with Z = A_{i+1,i} g^<_i, P = G^<_{i+1,i+1} X^H:
               G^<_ii = g^<_i + X P - G_{i,i+1} Z + (G_{i,i+1} Z)^H,
-              G^<_{i+1,i} = -G_{i+1,i+1} Z - P."""
+              G^<_{i+1,i} = -G_{i+1,i+1} Z - P.
+    G^> runs the same lesser recursion with Sigma^> in place of Sigma^<."""
     nb = dev.nb
     Ad, Au, Al = _A_blocks(dev, z, sigma_L, sigma_R, sigR_scat)
     inv = np.linalg.inv
@@ -411,22 +480,19 @@ def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_
     SigL[nb - 1] = SigL[nb - 1] + lead_lesser(sigma_R, fR)
     if sigL_scat is not None:
         SigL = [SigL[i] + sigL_scat[i] for i in range(nb)]
-    gl = [None] * nb
-    gl[0] = g[0] @ SigL[0] @ _H(g[0])
-    for i in range(1, nb):
-        gl[i] = g[i] @ (SigL[i] + Al[i - 1] @ gl[i - 1] @ _H(Al[i - 1])) @ _H(g[i])
-    GL_d = [None] * nb
-    GL_l = [None] * (nb - 1)
-    GL_d[nb - 1] = gl[nb - 1]
-    for i in range(nb - 2, -1, -1):
-        X = g[i] @ Au[i]
-        Z = Al[i] @ gl[i]
-        P = GL_d[i + 1] @ _H(X)
-        W = GR_u[i] @ Z
-        GL_d[i] = gl[i] + X @ P - W + _H(W)
-        GL_l[i] = -GR_d[i + 1] @ Z - P
+    GL_d, GL_l = _keldysh_sweep(g, GR_d, GR_u, Au, Al, SigL)
     out["GL_diag"] = np.stack(GL_d)
     out["GL_low"] = np.stack(GL_l) if nb > 1 else np.zeros((0, b, b), complex)
+    if greater:
+        SigG = [np.zeros((b, b), complex) for _ in range(nb)]
+        SigG[0] = SigG[0] + lead_greater(sigma_L, fL)
+        SigG[nb - 1] = SigG[nb - 1] + lead_greater(sigma_R, fR)
+        if sigR_scat is not None or sigL_scat is not None:
+            SigG = [SigG[i] + scattering_greater(None if sigR_scat is None else sigR_scat[i],
+                                                 None if sigL_scat is None else sigL_scat[i]) for i in range(nb)]
+        GG_d, GG_l = _keldysh_sweep(g, GR_d, GR_u, Au, Al, SigG)
+        out["GG_diag"] = np.stack(GG_d)
+        out["GG_low"] = np.stack(GG_l) if nb > 1 else np.zeros((0, b, b), complex)
     return out
 
 
@@ -504,8 +570,9 @@ def density(dev, weights, GL_diag_E, GL_low_E):
 # ---------------------------------------------------------------------------
 
 def solve_energy(dev, e, *, lesser=True, use_rgf=False, tol=1e-12, max_iter=100,
-                 sigma=None):
-    """OBC + Eq. (1)/(2) + observables for energy index ``e`` of ``dev``."""
+                 sigma=None, greater=False):
+    """OBC + Eq. (1)/(2) + observables for energy index ``e`` of ``dev`` (and G^>
+    with `greater`)."""
     z = dev.energy[e] + 1j * dev.eta
     if sigma is None:
         sL, sR, info = lead_self_energies(dev, z, tol, max_iter)
@@ -519,9 +586,9 @@ def solve_energy(dev, e, *, lesser=True, use_rgf=False, tol=1e-12, max_iter=100,
     if lesser and dev.sigL_base is not None:
         sL_scat = dev.sigL_scale[e][:, None, None] * dev.sigL_base
     if use_rgf:
-        out = rgf_blocks(dev, z, sL, sR, fL, fR, sR_scat, sL_scat)
+        out = rgf_blocks(dev, z, sL, sR, fL, fR, sR_scat, sL_scat, greater=greater and lesser)
     else:
-        out = greens_dense(dev, z, sL, sR, fL, fR, sR_scat, sL_scat)
+        out = greens_dense(dev, z, sL, sR, fL, fR, sR_scat, sL_scat, greater=greater and lesser)
         out["T_caroli"] = transmission_caroli(sL, sR, out["GR_corner"])
     out["sigma_L"], out["sigma_R"], out["obc"] = sL, sR, info
     out["T"] = transmission_g00(sL, out["GR_diag"][0])

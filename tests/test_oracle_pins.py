@@ -356,3 +356,64 @@ def test_config4_scattering_signs():
         assert np.linalg.eigvalsh(1j * (dev.sigR_scat[i] - H(dev.sigR_scat[i]))).min() >= -1e-14
         sl = dev.sigL_base[i]
         assert np.abs(sl + H(sl)).max() <= 1e-15     # Sigma^< anti-Hermitian
+
+
+# ---------------------------------------------------------------------------
+# G^> (the greater Green's function of the G^> output)
+# ---------------------------------------------------------------------------
+
+def test_greater_fluctuation_dissipation_in_equilibrium():
+    """Ballistic device, both leads at the same chemical potential: G^< = i f G (Gamma_L +
+    Gamma_R) G^A and G^> = -i (1 - f) G (Gamma_L + Gamma_R) G^A, so that
+    G^> = -((1 - f) / f) G^< exactly, block by block.  A wrong sign or a dropped (1 - f)
+    in Sigma^> fails it."""
+    dev = W.config1()
+    dev.mu_R = dev.mu_L
+    f = dev.f_L()
+    picked = [e for e in range(dev.ne) if 0.05 < f[e] < 0.95]
+    if not picked:   # widen kT until some energies sit inside the Fermi window
+        dev.kT = 0.5
+        f = dev.f_L()
+        picked = [e for e in range(dev.ne) if 0.05 < f[e] < 0.95]
+    assert picked
+    for e in picked[:4]:
+        out = O.solve_energy(dev, e, greater=True)
+        r = -(1.0 - f[e]) / f[e]
+        for kg, kl in (("GG_diag", "GL_diag"), ("GG_low", "GL_low")):
+            scale = np.abs(out[kg]).max()
+            assert scale > 0
+            assert np.abs(out[kg] - r * out[kl]).max() <= 1e-11 * scale, (e, kg)
+
+
+def test_greater_is_antihermitian_and_matches_spectral_identity():
+    """G^> = -(G^>)^H, and G^> - G^< = G^R (Sigma^R - Sigma^A) G^A = G^R - G^A + 2 i eta
+    G^R S G^A on every selected block (G^R - G^A also carries the eta broadening)."""
+    dev, z, sL, sR, fL, fR, sLs, out0 = _full_lesser_setup()
+    out = O.greens_dense(dev, z, sL, sR, fL, fR, dev.sigR_scat, sLs, keep_dense=True, greater=True)
+    GG, GL, G = out["GG"], out["GL"], out["G"]
+    assert np.abs(GG + H(GG)).max() <= 1e-13 * np.abs(GG).max()
+    _, S = O.dense_H_S(dev)
+    rhs = G - H(G) + 2j * dev.eta * G @ S @ H(G)
+    b, nb = dev.b, dev.nb
+    for i in range(nb):
+        s = slice(i * b, (i + 1) * b)
+        d = out["GG_diag"][i] - out["GL_diag"][i] - rhs[s, s]
+        assert np.abs(d).max() <= 1e-10 * np.abs(rhs).max()
+    for i in range(nb - 1):
+        s1, s0 = slice((i + 1) * b, (i + 2) * b), slice(i * b, (i + 1) * b)
+        d = out["GG_low"][i] - out["GL_low"][i] - rhs[s1, s0]
+        assert np.abs(d).max() <= 1e-10 * np.abs(rhs).max()
+
+
+def test_greater_block_recursion_matches_dense():
+    """The block recursion's G^> (the lesser sweeps run on Sigma^>) equals the dense
+    G^R Sigma^> G^A, with scattering and S != I.  Errors are measured against the
+    spectral function's scale max|G^R - G^A|, which bounds both G^< and G^> (far above
+    the chemical potentials G^> is many decades smaller)."""
+    dev = W.small_scattering_device(5, 6, 6, seed=31)
+    for e in range(dev.ne):
+        d = O.solve_energy(dev, e, greater=True)
+        r = O.solve_energy(dev, e, greater=True, use_rgf=True, sigma=(d["sigma_L"], d["sigma_R"]))
+        scale = np.abs(d["GR_diag"] - H(d["GR_diag"])).max()
+        for k in ("GG_diag", "GG_low", "GL_diag", "GL_low"):
+            assert np.abs(r[k] - d[k]).max() <= 1e-11 * scale, (e, k)
