@@ -182,6 +182,24 @@ negf_status negf_rgf_lesser(negf_ctx* ctx, const negf_system* sys, negf_precisio
                             void* GL_diag, void* GL_low,
                             int32_t* status, negf_stream stream);
 
+/* G^R, G^< and G^> (Eq. (2) for both B^<, B^>) in one fused sweep pair: the retarded
+ * sweep once, then the lesser recursion of negf_rgf_lesser run twice, on Sigma^< and on
+ *     Sigma^> = Sigma^>_scat - i (1 - f_L) Gamma_L - i (1 - f_R) Gamma_R,
+ *     Sigma^>_scat = Sigma^<_scat + Sigma^R_scat - (Sigma^R_scat)^H
+ * (the anti-Hermitian part of a retarded self-energy is Sigma^> - Sigma^<; for a
+ * scattering struct with per-block sigL_scale, the scale applies to Sigma^<_scat only).
+ * Arguments as negf_rgf_lesser, plus GG_diag ([sum ne*nb] blocks) and GG_low
+ * ([sum ne*(nb-1)] blocks, (i+1, i)), each device memory or NULL; with both NULL the
+ * call is negf_rgf_lesser.  G^>_{i,i+1} = -(G^>_{i+1,i})^H is not stored.  Work:
+ * 56 b^3 (G^R) + 2 x 72 b^3 (G^<, G^>) real flops per block. */
+negf_status negf_rgf_keldysh(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
+                             const void* sigma_L, const void* sigma_R,
+                             const double* f_L, const double* f_R,
+                             const negf_scattering* scat,
+                             void* GR_diag, void* GR_up, void* GR_low,
+                             void* GL_diag, void* GL_low, void* GG_diag, void* GG_low,
+                             int32_t* status, negf_stream stream);
+
 /* Observables (Sec. III: DOS, spectral current, current conservation), traces and sums
  * in FP64.  prec: the two block products of T (Gamma_L G_00 and G_00 Gamma_L) run in FP64
  * with NEGF_FP64 and NEGF_MIXED_TF32, on the digit-sliced tensor-core path (FP64-class,

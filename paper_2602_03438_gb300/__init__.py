@@ -5,4 +5,5 @@ include/negf.h; ``negf`` is its thin ctypes binding.
 """
 from . import negf  # noqa: F401
 from .negf import (FP64, MIXED, MIXED_TF32, Context, NegfError, Scattering, System, allocate_outputs,  # noqa: F401
-                   negf_obc, negf_observables, negf_rgf_lesser, negf_rgf_retarded, system_layout, upload)
+                   negf_obc, negf_observables, negf_rgf_keldysh, negf_rgf_lesser, negf_rgf_retarded,
+                   system_layout, upload)

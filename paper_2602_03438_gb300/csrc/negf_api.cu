@@ -142,6 +142,7 @@ struct AsmArgs {
   int i_diag;        // diagonal block index (A_ii and Sigma^<_ii), -1 => none
   int i_off;         // upper block index j (A_{j,j+1} and A_{j+1,j}), -1 => none
   zc *Adiag, *Aup, *Alow, *SigL;   // slot bases (unit stride b*b), each nullable
+  zc* SigG;                        // Sigma^>_ii slot (nullable)
   const zc *sigma_L, *sigma_R;     // lead self-energies of this device, [ne] blocks
   const double *fL, *fR;           // this device's occupations (nullable unless SigL)
 };
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   __shared__ zc tS[ASM_T][ASM_T + 1], tH[ASM_T][ASM_T + 1];
   const int i = a.i_diag, j = a.i_off;
-  const bool lead_lesser = a.SigL && (i == 0 || i == nb - 1);
+  const bool lead_lesser = (a.SigL || a.SigG) && (i == 0 || i == nb - 1);
   const zc* sg = (i == 0) ? a.sigma_L + e * bb : a.sigma_R + e * bb;
   const double fo = (i == 0) ? (a.fL ? a.fL[e] : 0.0) : (a.fR ? a.fR[e] : 0.0);
   // transposed tiles: (row c0 + ty + 8k, column r0 + tx) of S_up, H_up (for A_{j+1,j}) and
@@ -203,13 +204,19 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
       a.Alow[u * bb + rc] = zsub(zmul(z, s), zconj(tH[ty + 8 * k][tx]));
     }
   }
-  if (!a.SigL) return;
+  if (!a.SigL && !a.SigG) return;
   __syncthreads();
-  if (lead_lesser) {   // transposed tile of this lead's Sigma for its Sigma^H
+  // transposed tiles: this lead's Sigma (for Sigma^H) and, for Sigma^>, the scattering
+  // Sigma^R of block i (for Sigma^A)
+  const bool scat_adv = a.SigG && a.sc.sigR;
+  if (lead_lesser || scat_adv) {
 #pragma unroll
     for (int k = 0; k < ASM_T / 8; ++k) {
       const int rr = c0 + ty + 8 * k, cc = r0 + tx;
-      tS[tx][ty + 8 * k] = (rr < b && cc < b) ? sg[(long long)rr * b + cc] : zmake(0.0, 0.0);
+      const bool in = rr < b && cc < b;
+      if (lead_lesser) tS[tx][ty + 8 * k] = in ? sg[(long long)rr * b + cc] : zmake(0.0, 0.0);
+      if (scat_adv)
+        tH[tx][ty + 8 * k] = in ? a.sc.sigR[e * a.sc.e_stride + i * bb + (long long)rr * b + cc] : zmake(0.0, 0.0);
     }
   }
   __syncthreads();
@@ -223,17 +230,24 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
       const double f = a.sc.scale ? a.sc.scale[(long long)e * nb + i] : 1.0;
       v = zscale(a.sc.sigL[e * a.sc.e_stride + i * bb + rc], f);
     }
-    // lead lesser i f Gamma = -f (Sigma - Sigma^H)
+    // scattering Sigma^> = Sigma^< + Sigma^R - Sigma^A
+    zc vg = v;
+    if (scat_adv) vg = zadd(vg, zsub(a.sc.sigR[e * a.sc.e_stride + i * bb + rc], zconj(tH[ty + 8 * k][tx])));
+    // lead lesser i f Gamma = -f (Sigma - Sigma^H); lead greater -i (1 - f) Gamma = (1 - f) (Sigma - Sigma^H)
     if (lead_lesser) {
       const zc d = zsub(sg[rc], zconj(tS[ty + 8 * k][tx]));
       v = zsub(v, zscale(d, fo));
+      vg = zadd(vg, zscale(d, 1.0 - fo));
       if (nb == 1) {   // both leads on the one block
         const zc* sg2 = a.sigma_R + e * bb;
         const zc d2 = zsub(sg2[rc], zconj(sg2[(long long)c * b + r]));
-        v = zsub(v, zscale(d2, a.fR ? a.fR[e] : 0.0));
+        const double f2 = a.fR ? a.fR[e] : 0.0;
+        v = zsub(v, zscale(d2, f2));
+        vg = zadd(vg, zscale(d2, 1.0 - f2));
       }
     }
-    a.SigL[u * bb + rc] = v;
+    if (a.SigL) a.SigL[u * bb + rc] = v;
+    if (a.SigG) a.SigG[u * bb + rc] = vg;
   }
 }
 
@@ -409,8 +423,10 @@ struct RgfIO {
   const zc *sigma_L, *sigma_R;   // device-offset
   const double *fL, *fR;         // device-offset, nullable for retarded only
   zc *GRd, *GRu, *GRl, *GLd, *GLl;   // device-offset outputs, nullable
+  zc *GGd = nullptr, *GGl = nullptr; // device-offset G^> outputs, nullable
   int32_t* status;               // device-offset, nullable
   bool lesser;
+  bool greater = false;          // also G^> (with `lesser`)
 };
 
 negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& sc, const RgfIO& io, int e0,
@@ -426,11 +442,14 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   zc* Aup = slot(1);
   zc* Alow = slot(1);
   zc* SigL = io.lesser ? slot(1) : nullptr;
+  const bool greater = io.lesser && io.greater;
+  zc* SigG = greater ? slot(1) : nullptr;
   zc* T[4];
   for (int k = 0; k < 4; ++k) T[k] = slot(1);
   zc* Ybase = slot(std::max(nb - 1, 1));
   zc* gbase = io.GRd ? nullptr : slot(nb);
   zc* glbase = (io.lesser && !io.GLd) ? slot(nb) : nullptr;
+  zc* ggbase = (greater && !io.GGd) ? slot(nb) : nullptr;
   zc* gup_tmp = io.GRu ? nullptr : slot(1);
   if (zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0) > 0) {
     eng.inv_scratch = (void*)p;
@@ -449,7 +468,17 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     return io.GLd ? BMat{io.GLd + ((long long)e0 * nb + i) * bb, (long long)nb * bb}
                   : BMat{glbase + (long long)i * U * bb, bb};
   };
+  auto ggD = [&](int i) {
+    return io.GGd ? BMat{io.GGd + ((long long)e0 * nb + i) * bb, (long long)nb * bb}
+                  : BMat{ggbase + (long long)i * U * bb, bb};
+  };
   auto Yb = [&](int i) { return BMat{Ybase + (long long)i * U * bb, bb}; };
+  // the Keldysh kinds of this call: G^< and, with `greater`, G^> (the same recursion on
+  // Sigma^> in place of Sigma^<)
+  struct Kind { zc* sig; std::function<BMat(int)> D; zc* low; };
+  std::vector<Kind> kinds;
+  if (io.lesser) kinds.push_back(Kind{SigL, glD, io.GLl});
+  if (greater) kinds.push_back(Kind{SigG, ggD, io.GGl});
   auto offB = [&](zc* base, int i) { return BMat{base + ((long long)e0 * (nb - 1) + i) * bb, (long long)(nb - 1) * bb}; };
 
   AsmArgs a;
@@ -461,16 +490,16 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   for (int i = 0; i < nb; ++i) {
     a.i_diag = i;
     a.i_off = i - 1;
-    a.Adiag = Adiag; a.SigL = SigL;
+    a.Adiag = Adiag; a.SigL = SigL; a.SigG = SigG;
     a.Aup = (i > 0) ? Aup : nullptr;
     a.Alow = (i > 0) ? Alow : nullptr;
     ++ctx->launches;
     CU(assemble(a, s));
     if (i == 0) {
       CU(eng.inverse(gD(0), S1(Adiag), b, U, st, S1(T[1]), S1(T[2])));
-      if (io.lesser) {
-        CU(eng.gemm(S1(T[2]), gD(0), OP_N, S1(SigL), OP_N, ONE, NOMAT, ZERO, b, U));
-        CU(eng.gemm(glD(0), S1(T[2]), OP_N, gD(0), OP_H, ONE, NOMAT, ZERO, b, U));
+      for (const Kind& k : kinds) {
+        CU(eng.gemm(S1(T[2]), gD(0), OP_N, S1(k.sig), OP_N, ONE, NOMAT, ZERO, b, U));
+        CU(eng.gemm(k.D(0), S1(T[2]), OP_N, gD(0), OP_H, ONE, NOMAT, ZERO, b, U));
       }
       continue;
     }
@@ -478,16 +507,16 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     CU(eng.gemm(Yb(i - 1), S1(Alow), OP_N, gD(i - 1), OP_N, ONE, NOMAT, ZERO, b, U));
     CU(eng.gemm(S1(T[0]), Yb(i - 1), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, U));
     CU(eng.inverse(gD(i), S1(T[0]), b, U, st, S1(T[1]), S1(T[2])));
-    if (io.lesser) {
-      // g^<_i = g_i (Sigma^<_ii + A_{i,i-1} g^<_{i-1} A_{i,i-1}^H) g_i^H
-      CU(eng.gemm(S1(T[1]), S1(Alow), OP_N, glD(i - 1), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(S1(T[2]), S1(T[1]), OP_N, S1(Alow), OP_H, ONE, S1(SigL), ONE, b, U));
+    for (const Kind& k : kinds) {
+      // g^x_i = g_i (Sigma^x_ii + A_{i,i-1} g^x_{i-1} A_{i,i-1}^H) g_i^H   (x = <, >)
+      CU(eng.gemm(S1(T[1]), S1(Alow), OP_N, k.D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(S1(T[2]), S1(T[1]), OP_N, S1(Alow), OP_H, ONE, S1(k.sig), ONE, b, U));
       CU(eng.gemm(S1(T[3]), gD(i), OP_N, S1(T[2]), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(glD(i), S1(T[3]), OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(k.D(i), S1(T[3]), OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U));
     }
   }
   // ---------------- backward sweep
-  a.Adiag = nullptr; a.SigL = nullptr;
+  a.Adiag = nullptr; a.SigL = nullptr; a.SigG = nullptr;
   for (int i = nb - 2; i >= 0; --i) {
     a.i_diag = -1;
     a.i_off = i;
@@ -501,18 +530,18 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     CU(eng.gemm(Gup, X, OP_N, gD(i + 1), OP_N, MONE, NOMAT, ZERO, b, U));
     CU(eng.gemm(gD(i), Gup, OP_N, Yb(i), OP_N, MONE, gD(i), ONE, b, U));
     if (io.GRl) CU(eng.gemm(offB(io.GRl, i), gD(i + 1), OP_N, Yb(i), OP_N, MONE, NOMAT, ZERO, b, U));
-    if (io.lesser) {
+    for (const Kind& k : kinds) {
       const BMat Z = S1(T[1]), P = S1(T[2]), Wm = S1(T[3]);
-      // Z = A_{i+1,i} g^<_i;  P = G^<_{i+1,i+1} X^H;  W = G_{i,i+1} Z
-      CU(eng.gemm(Z, S1(Alow), OP_N, glD(i), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(P, glD(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U));
+      // Z = A_{i+1,i} g^x_i;  P = G^x_{i+1,i+1} X^H;  W = G_{i,i+1} Z   (x = <, >)
+      CU(eng.gemm(Z, S1(Alow), OP_N, k.D(i), OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(P, k.D(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U));
       CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U));
-      // G^<_ii = g^<_i + X P - W + W^H
-      CU(eng.gemm(glD(i), X, OP_N, P, OP_N, ONE, glD(i), ONE, b, U));
+      // G^x_ii = g^x_i + X P - W + W^H
+      CU(eng.gemm(k.D(i), X, OP_N, P, OP_N, ONE, k.D(i), ONE, b, U));
       ++ctx->launches;
-      CU(antiherm_update(glD(i), Wm, b, U, s));
-      // G^<_{i+1,i} = -G_{i+1,i+1} Z - P
-      if (io.GLl) CU(eng.gemm(offB(io.GLl, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U));
+      CU(antiherm_update(k.D(i), Wm, b, U, s));
+      // G^x_{i+1,i} = -G_{i+1,i+1} Z - P
+      if (k.low) CU(eng.gemm(offB(k.low, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U));
     }
   }
   return NEGF_OK;
@@ -520,9 +549,11 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
 
 size_t rgf_bytes_per_energy(int nb, int b, const RgfIO& io, int mixed) {
   const size_t blk = sizeof(zc) * (size_t)b * b;
-  size_t n = 3 + (io.lesser ? 1 : 0) + 4 + std::max(nb - 1, 1);
+  const bool greater = io.lesser && io.greater;
+  size_t n = 3 + (io.lesser ? 1 : 0) + (greater ? 1 : 0) + 4 + std::max(nb - 1, 1);
   if (!io.GRd) n += nb;
   if (io.lesser && !io.GLd) n += nb;
+  if (greater && !io.GGd) n += nb;
   if (!io.GRu) n += 1;
   size_t bytes = n * blk;
   bytes += zinv_scratch_bytes(b, 1, mixed ? 1 : 0);
@@ -1098,7 +1129,8 @@ negf_status negf_layout(const negf_system* sys, int64_t* out) {
 static negf_status rgf_common(Ctx* ctx, const negf_system* sys, negf_precision prec, const void* sigma_L,
                               const void* sigma_R, const double* f_L, const double* f_R,
                               const negf_scattering* scat, void* GR_diag, void* GR_up, void* GR_low,
-                              void* GL_diag, void* GL_low, int32_t* status, cudaStream_t s, bool lesser) {
+                              void* GL_diag, void* GL_low, int32_t* status, cudaStream_t s, bool lesser,
+                              void* GG_diag = nullptr, void* GG_low = nullptr) {
   if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
   Layout L;
   negf_status st = make_layout(ctx, sys, L);
@@ -1129,6 +1161,9 @@ static negf_status rgf_common(Ctx* ctx, const negf_system* sys, negf_precision p
     io.GRl = GR_low ? (zc*)GR_low + o[5] : nullptr;
     io.GLd = (lesser && GL_diag) ? (zc*)GL_diag + o[4] : nullptr;
     io.GLl = (lesser && GL_low) ? (zc*)GL_low + o[5] : nullptr;
+    io.GGd = (lesser && GG_diag) ? (zc*)GG_diag + o[4] : nullptr;
+    io.GGl = (lesser && GG_low) ? (zc*)GG_low + o[5] : nullptr;
+    io.greater = lesser && (GG_diag || GG_low);
     io.status = status ? status + o[2] : nullptr;
     io.lesser = lesser;
     const size_t per = rgf_bytes_per_energy(dv.nb, dv.b, io, eng.mixed);
@@ -1160,6 +1195,14 @@ negf_status negf_rgf_lesser(negf_ctx* c, const negf_system* sys, negf_precision 
                             void* GL_low, int32_t* status, negf_stream stream) {
   return rgf_common(reinterpret_cast<Ctx*>(c), sys, prec, sigma_L, sigma_R, f_L, f_R, scat, GR_diag, GR_up,
                     GR_low, GL_diag, GL_low, status, (cudaStream_t)stream, true);
+}
+
+negf_status negf_rgf_keldysh(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* sigma_L,
+                             const void* sigma_R, const double* f_L, const double* f_R,
+                             const negf_scattering* scat, void* GR_diag, void* GR_up, void* GR_low, void* GL_diag,
+                             void* GL_low, void* GG_diag, void* GG_low, int32_t* status, negf_stream stream) {
+  return rgf_common(reinterpret_cast<Ctx*>(c), sys, prec, sigma_L, sigma_R, f_L, f_R, scat, GR_diag, GR_up,
+                    GR_low, GL_diag, GL_low, status, (cudaStream_t)stream, true, GG_diag, GG_low);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,7 +29,8 @@ MIXED = 1
 MIXED_TF32 = 2
 
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
-           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_observables", "negf_profile_enable",
+           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_rgf_keldysh", "negf_observables",
+           "negf_profile_enable",
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
            "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
            "negf_mlp_forward", "negf_mlp_train_step"]
@@ -90,6 +91,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                       vp, vp, vp, vp, vp]
     lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                     vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_rgf_keldysh.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
+                                     vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_observables.argtypes = [vp, C.POINTER(_System), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_block_gemm.argtypes = [vp, C.c_int, i32, i32, i32, i32, vp, vp, C.c_int64, vp, C.c_int64, vp, vp,
                                     C.c_int64, vp, C.c_int64, vp]
@@ -306,6 +309,17 @@ def negf_rgf_lesser(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R,
                                       _stream(stream)))
 
 
+def negf_rgf_keldysh(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, scat=None, GR_diag=None,
+                     GR_up=None, GR_low=None, GL_diag=None, GL_low=None, GG_diag=None, GG_low=None, status=None,
+                     stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_keldysh(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(sigma_R), _ptr(f_L),
+                                       _ptr(f_R), C.byref(sc) if sc is not None else None, _ptr(GR_diag),
+                                       _ptr(GR_up), _ptr(GR_low), _ptr(GL_diag), _ptr(GL_low), _ptr(GG_diag),
+                                       _ptr(GG_low), _ptr(status), _stream(stream)))
+
+
 def negf_observables(ctx: Context, sys: System, sigma_L=None, e_weight=None, GR_diag=None, GR_up=None,
                      GR_low=None, GL_diag=None, GL_low=None, T=None, dos=None, current=None, density=None,
                      stream=None, prec: int = FP64):
@@ -319,7 +333,7 @@ def negf_observables(ctx: Context, sys: System, sigma_L=None, e_weight=None, GR_
 # output allocation helper (torch is the allocator)
 # ---------------------------------------------------------------------------
 
-def allocate_outputs(sys: System, lesser=True, device="cuda", want_up_low=True):
+def allocate_outputs(sys: System, lesser=True, device="cuda", want_up_low=True, greater=False):
     L = sys.layout()
     tot = L[-1]
     z = lambda n: torch.empty(int(n), dtype=torch.complex128, device=device)
@@ -338,6 +352,8 @@ def allocate_outputs(sys: System, lesser=True, device="cuda", want_up_low=True):
         out.update(GL_diag=z(tot[4]), GL_low=z(tot[5]),
                    current=torch.zeros(int(tot[6]), dtype=torch.float64, device=device),
                    density=torch.zeros(int(tot[7]), dtype=torch.float64, device=device))
+        if greater:
+            out.update(GG_diag=z(tot[4]), GG_low=z(tot[5]))
     return out
 
 

@@ -50,8 +50,12 @@ def test_config2_full_launch_sampled_energies(P):
         assert int((out["obc_status"] != 0).sum()) == 0
         assert int((out["status"] != 0).sum()) == 0
         nb, b = dev.nb, dev.b
-        # in-band (|E| < 0.5, near-resonant blocks) and out-of-band energies
-        for e in [2, 430, 470, 511, 540, 600, 1021]:
+        # in-band (|E| < 0.5, near-resonant blocks; 528 is near the peak of the current)
+        # and out-of-band energies
+        sample = [2, 430, 470, 511, 528, 540, 600, 1021]
+        J_got, J_ref, n_ref = [], [], np.zeros(nb * b)
+        wh = dev.weights()
+        for e in sample:
             sL = out["sigma_L"].view(-1, b, b)[e].cpu().numpy()
             sR = out["sigma_R"].view(-1, b, b)[e].cpu().numpy()
             sub = dev.truncated(energies=[e])
@@ -69,6 +73,28 @@ def test_config2_full_launch_sampled_energies(P):
             assert abs(out["T"][e].item() - ref["T"]) <= 4 * TOL_MIXED * tscale
             smax = max(np.linalg.norm(dev.S_diag[0]) if dev.S_diag is not None else 1.0, 1.0)
             assert abs(out["dos"][e].item() - ref["dos"]) <= TOL_MIXED * gmax * smax * (3 * nb) / np.pi
+            J_got.append(out["current"].view(-1, nb - 1)[e].cpu().numpy())
+            J_ref.append(ref["J"])
+            n_ref += wh[e] * ref["n_E"]
+        # mixed current against the oracle, scalar reading: |dJ| / max(|J|, 1e-3 max |J|)
+        J_got, J_ref = np.array(J_got), np.array(J_ref)
+        floor = 1e-3 * np.abs(J_ref).max()
+        assert floor > 0
+        assert (np.abs(J_got - J_ref) / np.maximum(np.abs(J_ref), floor)).max() <= TOL_MIXED
+        # mixed density of the sampled energies (the grid's weights), normwise: the sampled
+        # blocks of the full launch go through negf_observables as a sub-batch
+        sub = dev.truncated(energies=sample)
+        s2 = P.upload(sub)
+        o2 = P.allocate_outputs(s2)
+        sel = torch.tensor(sample, device="cuda")
+        for key in ("GL_diag", "GL_low"):
+            o2[key].copy_(out[key].view(dev.ne, -1)[sel].reshape(-1))
+        w2 = torch.from_numpy(wh[sample]).cuda()
+        P.negf_observables(ctx, s2, None, w2, None, None, None, o2["GL_diag"], o2["GL_low"], None, None,
+                           None, o2["density"], prec=P.MIXED)
+        assert ctx.sync() == 0
+        n_got = o2["density"].cpu().numpy()
+        assert np.linalg.norm(n_got - n_ref) <= TOL_MIXED * np.linalg.norm(n_ref)
     finally:
         ctx.close()
 
