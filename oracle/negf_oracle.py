@@ -36,7 +36,7 @@ __all__ = [
     "assemble_sigma_lesser", "assemble_sigma_greater",
     "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
     "interface_current", "density", "solve_energy", "retarded_check", "surface_newton_warm",
-    "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf",
+    "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf", "partitioned_retarded",
 ]
 
 
@@ -494,6 +494,108 @@ def rgf_blocks(dev, z, sigma_L, sigma_R, fL=None, fR=None, sigR_scat=None, sigL_
         out["GG_diag"] = np.stack(GG_d)
         out["GG_low"] = np.stack(GG_l) if nb > 1 else np.zeros((0, b, b), complex)
     return out
+
+
+# ---------------------------------------------------------------------------
+# partitioned selected inversion (Sec. II and Fig. 3: Schur complements of P
+# partitions, a reduced system solved sequentially, local reconstruction)
+# ---------------------------------------------------------------------------
+
+def _rgf_retarded_from_blocks(Ad, Au, Al):
+    """G^R diagonal, upper and lower blocks of a BT matrix given by its blocks
+    (the textbook recursion of ``rgf_blocks``, retarded part)."""
+    nb = len(Ad)
+    inv = np.linalg.inv
+    g = [None] * nb
+    g[0] = inv(Ad[0])
+    for i in range(1, nb):
+        g[i] = inv(Ad[i] - Al[i - 1] @ g[i - 1] @ Au[i - 1])
+    Gd, Gu, Gl = [None] * nb, [None] * (nb - 1), [None] * (nb - 1)
+    Gd[nb - 1] = g[nb - 1]
+    for i in range(nb - 2, -1, -1):
+        X = g[i] @ Au[i]
+        Y = Al[i] @ g[i]
+        Gu[i] = -X @ Gd[i + 1]
+        Gl[i] = -Gd[i + 1] @ Y
+        Gd[i] = g[i] - Gu[i] @ Y
+    return Gd, Gu, Gl
+
+
+def partitioned_retarded(dev, z, sigma_L, sigma_R, P, sigR_scat=None):
+    """Selected blocks of G^R by partitioning the BT matrix (nb = P L blocks, L >= 2).
+
+    Partition p holds blocks pL .. pL+L-1.  Its interior blocks pL .. pL+L-2 are
+    eliminated downward (Schur complements), keeping its last block e_p = pL+L-1 and
+    the previous partition's last block e_(p-1) (its top neighbour) as boundaries:
+      D_0 = A_(pL,pL), F_(a,0) = A_(pL-1,pL), F_(0,a) = A_(pL,pL-1)  (F = 0 for p = 0);
+      for k (block i, next block j = i+1):  g_k = D_k^{-1},
+        Y_k = A_ji g_k,  X_k = g_k A_ij,  Xa_k = F_(a,k) g_k,  Wa_k = g_k F_(k,a),
+        D_j = A_jj - Y_k A_ij,  F_(a,j) = -Xa_k A_ij,  F_(j,a) = -Y_k F_(k,a),
+        dD_a -= Xa_k F_(k,a).
+    The reduced system over the boundaries e_0 .. e_(P-1) is BT with diagonal
+    D_(e_p) + dD_a of partition p+1 and couplings F_(a,b), F_(b,a) of partition p+1;
+    its inverse (the textbook recursion) gives G on the boundaries.  Each partition
+    then rebuilds its interior from j = e_p down to pL, with a = e_(p-1):
+      G_jk = -(G_ja Xa_k + G_jj Y_k),  G_ak = -(G_aa Xa_k + G_aj Y_k),
+      G_kj = -(Wa_k G_aj + X_k G_jj),  G_ka = -(Wa_k G_aa + X_k G_ja),
+      G_kk = g_k - (Wa_k G_ak + X_k G_jk).
+    With P = 1 this is the textbook recursion itself."""
+    nb, b = dev.nb, dev.b
+    if P < 1 or nb % P or nb // P < 2:
+        raise ValueError("need nb = P L with L >= 2")
+    L = nb // P
+    Ad, Au, Al = _A_blocks(dev, z, sigma_L, sigma_R, sigR_scat)
+    inv = np.linalg.inv
+    Z = np.zeros((b, b), dtype=np.complex128)
+    parts = []
+    for p in range(P):
+        s0 = p * L
+        has_a = p > 0
+        D = Ad[s0]
+        Fak = Au[s0 - 1] if has_a else Z
+        Fka = Al[s0 - 1] if has_a else Z
+        dDa = Z
+        st = dict(g=[], Y=[], X=[], Xa=[], Wa=[])
+        for k in range(L - 1):
+            i, j = s0 + k, s0 + k + 1
+            gk = inv(D)
+            Yk, Xk = Al[i] @ gk, gk @ Au[i]
+            Xak, Wak = Fak @ gk, gk @ Fka
+            for key, v in (("g", gk), ("Y", Yk), ("X", Xk), ("Xa", Xak), ("Wa", Wak)):
+                st[key].append(v)
+            D = Ad[j] - Yk @ Au[i]
+            dDa = dDa - Xak @ Fka
+            Fak, Fka = -Xak @ Au[i], -Yk @ Fka
+        st.update(Db=D, dDa=dDa, Fab=Fak, Fba=Fka)
+        parts.append(st)
+    # reduced system over e_0 .. e_(P-1)
+    Rd = [parts[r]["Db"] + (parts[r + 1]["dDa"] if r + 1 < P else Z) for r in range(P)]
+    Ru = [parts[r + 1]["Fab"] for r in range(P - 1)]
+    Rl = [parts[r + 1]["Fba"] for r in range(P - 1)]
+    Gr_d, Gr_u, Gr_l = _rgf_retarded_from_blocks(Rd, Ru, Rl)
+    GRd, GRu, GRl = [None] * nb, [None] * (nb - 1), [None] * (nb - 1)
+    for p in range(P):
+        s0, st = p * L, parts[p]
+        has_a = p > 0
+        Gjj = Gr_d[p]
+        GRd[s0 + L - 1] = Gjj
+        Gaa = Gr_d[p - 1] if has_a else Z
+        Gaj = Gr_u[p - 1] if has_a else Z
+        Gja = Gr_l[p - 1] if has_a else Z
+        for k in range(L - 2, -1, -1):
+            i = s0 + k
+            Gjk = -(Gja @ st["Xa"][k] + Gjj @ st["Y"][k])
+            Gak = -(Gaa @ st["Xa"][k] + Gaj @ st["Y"][k])
+            Gkj = -(st["Wa"][k] @ Gaj + st["X"][k] @ Gjj)
+            Gka = -(st["Wa"][k] @ Gaa + st["X"][k] @ Gja)
+            Gkk = st["g"][k] - (st["Wa"][k] @ Gak + st["X"][k] @ Gjk)
+            GRd[i], GRu[i], GRl[i] = Gkk, Gkj, Gjk
+            Gjj, Gja, Gaj = Gkk, Gka, Gak
+        if has_a:
+            GRu[s0 - 1], GRl[s0 - 1] = Gaj, Gja
+    return dict(GR_diag=np.stack(GRd),
+                GR_up=np.stack(GRu) if nb > 1 else np.zeros((0, b, b), complex),
+                GR_low=np.stack(GRl) if nb > 1 else np.zeros((0, b, b), complex))
 
 
 # ---------------------------------------------------------------------------

@@ -417,3 +417,41 @@ def test_greater_block_recursion_matches_dense():
         scale = np.abs(d["GR_diag"] - H(d["GR_diag"])).max()
         for k in ("GG_diag", "GG_low", "GL_diag", "GL_low"):
             assert np.abs(r[k] - d[k]).max() <= 1e-11 * scale, (e, k)
+
+
+# ---------------------------------------------------------------------------
+# partitioned selected inversion (Fig. 3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nb,P", [(4, 2), (6, 3), (8, 4), (8, 2), (9, 3), (6, 1)])
+def test_partitioned_retarded_matches_dense_inverse(nb, P):
+    """Partitioned elimination + reduced system + reconstruction gives the selected
+    blocks of the dense inverse (with scattering, S != I, and leads)."""
+    dev = W.small_scattering_device(nb, 5, 3, seed=60 + nb + P, overlap=True, strength=0.05)
+    for e in range(dev.ne):
+        z = dev.energy[e] + 1j * dev.eta
+        sL, sR, _ = O.lead_self_energies(dev, z)
+        d = O.greens_dense(dev, z, sL, sR, sigR_scat=dev.sigR_scat)
+        r = O.partitioned_retarded(dev, z, sL, sR, P, sigR_scat=dev.sigR_scat)
+        scale = np.abs(d["GR_diag"]).max()
+        for k in ("GR_diag", "GR_up", "GR_low"):
+            assert np.abs(r[k] - d[k]).max() <= 1e-11 * scale, (k, e)
+
+
+def test_partitioned_retarded_one_partition_is_the_block_recursion():
+    dev = W.small_scattering_device(5, 4, 2, seed=71)
+    z = dev.energy[1] + 1j * dev.eta
+    sL, sR, _ = O.lead_self_energies(dev, z)
+    a = O.partitioned_retarded(dev, z, sL, sR, 1, sigR_scat=dev.sigR_scat)
+    b = O.rgf_blocks(dev, z, sL, sR, sigR_scat=dev.sigR_scat)
+    for k in ("GR_diag", "GR_up", "GR_low"):
+        assert np.abs(a[k] - b[k]).max() <= 1e-12 * np.abs(b[k]).max()
+
+
+def test_partitioned_retarded_rejects_uneven_partitions():
+    dev = W.small_scattering_device(5, 4, 1, seed=72)
+    z = dev.energy[0] + 1j * dev.eta
+    with pytest.raises(ValueError):
+        O.partitioned_retarded(dev, z, np.zeros((4, 4)), np.zeros((4, 4)), 2)
+    with pytest.raises(ValueError):
+        O.partitioned_retarded(dev.truncated(nb=4), z, np.zeros((4, 4)), np.zeros((4, 4)), 4)
