@@ -28,7 +28,8 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-# BF16 slice-pair products per complex product in the sliced GEMM (8 digits, s + t <= 9)
+# BF16 slice-pair products per complex product in the sliced GEMM: NS (NS + 1) / 2 for NS
+# digits per value (s + t <= NS + 1); set from the loaded library by run_gpu
 OZ_SLICE_PAIRS = 36.0
 
 METRIC = ("energy points/sec (G^R+G^< RGF, nb=64, bs=128) mixed vs FP64 on 1 GB300 at ≤1e-6 rel")
@@ -137,9 +138,13 @@ def measured_peaks():
 def roofline_for(cls, stats, peaks, peak_src, sustained=True):
     """Roofline object for one kernel class from live event timings.
 
-    gemm_tc : 3-term TF32 split complex GEMM.  achieved = useful complex flops
-              (8 n^3 per product) / time; peak = TF32 dense peak / 3, the TF32
-              peak taken as the bf16 peak x (1.1 / 2.25) (nominal ratio).
+    gemm_oz, gemm_tc : complex block products on the tensor cores.  achieved =
+              useful complex flops (8 n^3 per product) / time; peak = the useful peak
+              of a complex product on the tensor cores, TF32 dense peak / 3 (a complex
+              product costs 24 n^3 TF32 flops as a 3-term split), the TF32 peak taken as
+              the bf16 peak x (1.1 / 2.25) (nominal ratio).  For the sliced product the
+              executed BF16 work (OZ_SLICE_PAIRS x useful) against the bf16 peak is
+              reported beside it (tensor-pipe occupancy by the emulation).
     gemm_f64, inv_f64: FP64 pipe ("alu"), peak 1.25 TFLOP/s nominal.
     inv_f32 : FP32 CUDA cores ("alu"), peak 152 SM x 128 lanes x 2 x 2.07 GHz."""
     ms = stats["ms"]
@@ -148,14 +153,15 @@ def roofline_for(cls, stats, peaks, peak_src, sustained=True):
     per_launch_s = ms / 1e3 / n
     achieved = (fl / n) / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
     bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+    extra = {}
     if cls == "gemm_oz":
-        # 8-digit slicing: 36 BF16 slice-pair products (s + t <= 9) per complex product
-        # (n = 128 tiles exactly); tensor flops = 36 x the 8 n^3 useful flops, against
-        # the BF16 peak
-        achieved *= OZ_SLICE_PAIRS
-        bound, peak, unit = "tensor", bf16, "TFLOP/s"
-        note = (f"BF16 tensor flops executed ({OZ_SLICE_PAIRS:.0f} x useful) vs bf16 "
-                f"{'sustained' if sustained else 'burst'} {peak_src} peak")
+        bound, peak, unit = "tensor", bf16 * (1.1 / 2.25) / 3.0, "TFLOP/s"
+        note = (f"useful complex flops (8 n^3 per product) vs TF32 peak/3 (TF32 = bf16 "
+                f"{'sustained' if sustained else 'burst'} {peak_src} x 1.1/2.25)")
+        extra = {"executed_bf16_tflops": achieved * OZ_SLICE_PAIRS,
+                 "executed_bf16_frac": achieved * OZ_SLICE_PAIRS / bf16,
+                 "executed_note": f"{OZ_SLICE_PAIRS:.0f} BF16 slice-pair products per complex product "
+                                  f"vs bf16 {'sustained' if sustained else 'burst'} {peak_src} peak"}
     elif cls == "gemm_tc":
         bound, peak, unit = "tensor", bf16 * (1.1 / 2.25) / 3.0, "TFLOP/s"
         note = f"useful complex flops vs TF32 peak/3 (TF32 = bf16 {peak_src} x 1.1/2.25)"
@@ -170,10 +176,12 @@ def roofline_for(cls, stats, peaks, peak_src, sustained=True):
         achieved = (stats["bytes"] / n) / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
         note = f"HBM ({peak_src})"
     useful = (fl / n) / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
-    return {"kernel": cls, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "useful_tflops": useful,
-            "frac": achieved / peak if peak else None, "launches": stats["launches"],
-            "avg_launch_ms": ms / n, "peak_source": f"{peak_src}: {note}"}
+    out = {"kernel": cls, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "useful_tflops": useful,
+           "frac": achieved / peak if peak else None, "launches": stats["launches"],
+           "avg_launch_ms": ms / n, "peak_source": f"{peak_src}: {note}"}
+    out.update(extra)
+    return out
 
 
 def traffic_for(cls):
@@ -282,12 +290,42 @@ def rel_block_err(a, b, nblk):
     return float((num / den).max())
 
 
+def observables_vs_fp64(P, ctx, s2, o2, out, idx, w, ne, nb, b):
+    """Mixed-vs-FP64 error of the current and the density on the sampled energies.
+    The mixed blocks of those energies are gathered into a copy of the FP64 run's
+    buffers and both sets go through negf_observables.  J: max over energies and
+    interfaces of |dJ| / max(|J64|, 1e-3 max |J64|) (the scalar reading); n: the
+    density summed over the sample with the grid's weights, normwise."""
+    import torch
+    sel = torch.from_numpy(idx).cuda()
+    o3 = {kk: (v.clone() if v is not None else None) for kk, v in o2.items()}
+    for key, nblk in (("GL_diag", nb), ("GL_low", nb - 1)):
+        o3[key].copy_(out[key].view(ne, -1)[sel].reshape(-1))
+    ws = w[sel].contiguous()
+    res = {}
+    for o in (o2, o3):
+        P.negf_observables(ctx, s2, o["sigma_L"], ws, o["GR_diag"], o["GR_up"], o["GR_low"], o["GL_diag"],
+                           o["GL_low"], None, None, o["current"], o["density"], prec=P.FP64)
+    torch.cuda.synchronize()
+    J64, Jm = o2["current"].cpu().numpy(), o3["current"].cpu().numpy()
+    n64, nm = o2["density"].cpu().numpy(), o3["density"].cpu().numpy()
+    floor = 1e-3 * max(np.abs(J64).max(), 1e-300)
+    res["J"] = float((np.abs(Jm - J64) / np.maximum(np.abs(J64), floor)).max())
+    res["n"] = float(np.linalg.norm(nm - n64) / max(np.linalg.norm(n64), 1e-300))
+    res["J_max_abs"] = float(np.abs(J64).max())
+    del o3
+    return res
+
+
 def run_gpu(args):
     import torch
     import paper_2602_03438_gb300 as P
 
+    global OZ_SLICE_PAIRS
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    ns = P.negf.sliced_digits()
+    OZ_SLICE_PAIRS = ns * (ns + 1) / 2.0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
@@ -402,8 +440,10 @@ def run_gpu(args):
             num = torch.stack([nums[x] for x in keys]).amax(0)
             den = torch.stack([dens[x] for x in keys]).amax(0).clamp_min(1e-300)
             joint[g] = float((num / den).max().item())
+        obs_err = observables_vs_fp64(P, ctx, s2, o2, out, idx, w, ne, nb, b)
         cmp = {"fp64_rgf_value": fp64_value, "fp64_energies": k, "speedup_vs_fp64": rgf_value / world / fp64_value,
-               "err_vs_fp64_max": max(joint.values()), "err_vs_fp64": joint, "err_per_block_family": errs}
+               "err_vs_fp64_max": max(max(joint.values()), obs_err["J"], obs_err["n"]), "err_vs_fp64": joint,
+               "err_observables_vs_fp64": obs_err, "err_per_block_family": errs}
         del o2, s2
 
     # ---- end to end through host buffers: H2D inputs, the path, D2H observables
@@ -454,7 +494,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {P.MIXED: "bf16 8-digit slices (exact fp32 accumulate) + f32 inverse + f64",
+        "dtype": {P.MIXED: f"bf16 {ns}-digit slices (exact fp32 accumulate) + f32 inverse + f64",
                   P.MIXED_TF32: "tf32x3 + f32 inverse + f64", P.FP64: "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": f"config 2: ballistic batched RGF, nb={nb}, b={b}, {ne} energies/GPU in [-3,3], "
@@ -477,6 +517,60 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_probe_partitioned(args):
+    """Few energies of a long device: --probe partitioned times the sequential G^R sweep
+    (negf_rgf_retarded) against the partitioned selected inversion (negf_rgf_partitioned)
+    for P = 1, 2, 4, 8, 16 on `ne_cap` energies of the config-2 device lengthened to `nb`
+    blocks (default 128), Sigma_OBC precomputed, in the precision of --prec.  Prints one
+    JSON line with ms per call and energy points/s per variant and the largest normwise
+    G^R difference to the sequential result; not a bench line."""
+    import torch
+    import paper_2602_03438_gb300 as P
+    torch.cuda.set_device(0)
+    prec = {"mixed": P.MIXED, "fp64": P.FP64, "mixed_tf32": P.MIXED_TF32}[args.prec]
+    nb = args.nb if args.nb != 64 else 128
+    full = W.config2(nb=nb, b=args.b, ne=args.ne)
+    dev = full.truncated(energies=np.linspace(0, full.ne - 1, args.ne_cap).round().astype(int))
+    ctx = P.Context(0, int(args.workspace_gb * (1 << 30)))
+    sys_ = P.upload(dev)
+    out = P.allocate_outputs(sys_, lesser=False)
+    P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"], prec=P.MIXED)
+    ref = {k: torch.empty_like(out[k]) for k in ("GR_diag", "GR_up", "GR_low")}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    seq = lambda: P.negf_rgf_retarded(ctx, sys_, prec, out["sigma_L"], out["sigma_R"], None, ref["GR_diag"],
+                                      ref["GR_up"], ref["GR_low"], out["status"])
+    res = {"sequential": {"ms_per_call": timed(seq)}}
+    for parts in (1, 2, 4, 8, 16):
+        if nb % parts or nb // parts < 2:
+            continue
+        fn = lambda: P.negf_rgf_partitioned(ctx, sys_, prec, parts, out["sigma_L"], out["sigma_R"], None,
+                                            out["GR_diag"], out["GR_up"], out["GR_low"], out["status"])
+        ms = timed(fn)
+        num = max(float(torch.linalg.vector_norm(out[k] - ref[k])) for k in ref)
+        den = max(float(torch.linalg.vector_norm(ref[k])) for k in ref)
+        res[f"P={parts}"] = {"ms_per_call": ms, "diff_vs_sequential": num / den}
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the probe")
+    for v in res.values():
+        v["energy_points_per_s"] = dev.ne / (v["ms_per_call"] / 1e3)
+    print(json.dumps({"probe": "partitioned", "nb": nb, "b": args.b, "energies": dev.ne,
+                      "precision": args.prec, "what": "G^R selected blocks, Sigma_OBC precomputed",
+                      "results": res}))
+    ctx.close()
 
 
 def run_probe(args):
@@ -634,12 +728,14 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", choices=["gemm", "inverse"], default=None)
+    ap.add_argument("--probe", choices=["gemm", "inverse", "partitioned"], default=None)
     ap.add_argument("--workload", choices=["config3", "config4"], default=None)
     ap.add_argument("--devices", type=int, default=16)
     ap.add_argument("--ne-cap", type=int, default=64)
     args = ap.parse_args(argv)
-    if args.probe:
+    if args.probe == "partitioned":
+        run_probe_partitioned(args)
+    elif args.probe:
         run_probe(args)
     elif args.workload:
         run_workload(args)

@@ -65,9 +65,11 @@ typedef enum {
 typedef enum {
   NEGF_FP64 = 0,       /* every product, inverse and reduction in FP64                      */
   NEGF_MIXED = 1,      /* block products on the BF16 tensor cores with exact FP32
-                          accumulation of 7-bit digit slices (FP64-class, ~2^-55 of the
-                          row/column scales, 16 <= b <= 512, K in exact passes of 256; FP64 FMA otherwise); block inverses in FP32 + two refinement steps
-                          whose residual uses the same product; I/O stays complex128        */
+                          accumulation of 7-bit digit slices (FP64-class: ~2^-55 of the
+                          row/column scales with the default 8 digits, see
+                          negf_sliced_digits; 16 <= b <= 512, K in exact passes of 256;
+                          FP64 FMA otherwise); block inverses in FP32 + two refinement
+                          steps whose residual uses the same product; I/O complex128        */
   NEGF_MIXED_TF32 = 2  /* block products as 3-term TF32 splits (hi*hi + hi*lo + lo*hi) on
                           the tensor cores, FP32 accumulate in TMEM (~1e-6 relative per
                           128-wide product); inverses FP32 + refinement with an FP64
@@ -133,7 +135,7 @@ negf_status negf_layout(const negf_system* sys, int64_t* out);
  * prec: NEGF_FP64 runs every product in FP64; NEGF_MIXED runs the products of the
  * decimation, the residuals and the Newton steps on the digit-sliced BF16 tensor-core
  * path (FP64-class: exact FP32 accumulation of 7-bit slices, ~2^-55 of the row/column
- * scales) when 16 <= b <= 512, keeping every inverse in FP64; NEGF_MIXED_TF32 is
+ * scales with 8 digits) when 16 <= b <= 512, keeping every inverse in FP64; NEGF_MIXED_TF32 is
  * treated as NEGF_FP64 (a TF32 product is far too coarse for the 1e-10 residual).
  *
  * Warm start (optional, per lead side): with g0_L and/or g0_R given, that side
@@ -181,6 +183,24 @@ negf_status negf_rgf_lesser(negf_ctx* ctx, const negf_system* sys, negf_precisio
                             void* GR_diag, void* GR_up, void* GR_low,
                             void* GL_diag, void* GL_low,
                             int32_t* status, negf_stream stream);
+
+/* Selected blocks of G^R (Eq. (1)) by partitioned selected inversion (Sec. II and
+ * Fig. 3: Schur complements of P partitions, a reduced system solved sequentially,
+ * local reconstruction), for few energies and long devices: every step is one batched
+ * launch over (energy, partition) units instead of energies alone.  Each device's nb
+ * must be P L with L >= 2 (else NEGF_ERR_ARG; P = 1 is the plain recursion).  Partition
+ * p eliminates blocks pL .. pL+L-2 downward, coupled to the previous partition's last
+ * block; the last blocks e_p = pL+L-1 form a P-block BT system; the interiors are then
+ * rebuilt from its inverse.  Work per interior block: 18 block products and 1 inverse
+ * (152 b^3 real flops, against 56 b^3 for the plain recursion) for a sequential depth of
+ * ~2 nb/P + 2 P steps instead of 2 nb.  Arguments as negf_rgf_retarded, with GR_diag,
+ * GR_up and GR_low all required (device memory); status (device int32 [sum ne] or NULL)
+ * gets the worst code of the energy's partitions.  The workspace holds ~(4 nb + 17 P)
+ * blocks per energy; energies are chunked to fit it. */
+negf_status negf_rgf_partitioned(negf_ctx* ctx, const negf_system* sys, negf_precision prec, int32_t P,
+                                 const void* sigma_L, const void* sigma_R, const negf_scattering* scat,
+                                 void* GR_diag, void* GR_up, void* GR_low, int32_t* status,
+                                 negf_stream stream);
 
 /* G^R, G^< and G^> (Eq. (2) for both B^<, B^>) in one fused sweep pair: the retarded
  * sweep once, then the lesser recursion of negf_rgf_lesser run twice, on Sigma^< and on
@@ -273,6 +293,12 @@ negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t opA, int32
                                     const void* A, int64_t a_stride, const void* B, int64_t b_stride,
                                     const double* beta, const void* C, int64_t c_stride, void* D,
                                     int64_t d_stride, int32_t* status, negf_stream stream);
+
+/* Digits per value of the NEGF_MIXED sliced product in this build (NEGF_OZ_DIGITS at
+ * compile time, 6..8; 8 by default): NS digits of 7 bits give an error of ~2^(1 - 7 NS)
+ * of the row x column scales and NS (NS + 1) / 2 BF16 slice-pair products per complex
+ * product.  Not a paper operation: build introspection for measurement. */
+int32_t negf_sliced_digits(void);
 
 /* Kernel timing (the tracing facility).  When enabled, every launch of the
  * block-GEMM and block-inverse kernels is bracketed by CUDA events recorded on

@@ -8,26 +8,29 @@
 // blocks of the RGF at eta = 1e-6 amplify that by ~1e4.  Integer-valued operands,
 // however, accumulate exactly as long as every partial sum stays below 2^24.
 //
-// Scheme (error-free slicing in the manner of Ozaki et al.):
+// Scheme (error-free slicing in the manner of Ozaki et al.), with NS digits per value
+// (NEGF_OZ_DIGITS, 6..8; 8 by default):
 //  * every row m of op(A') and column j of op(B') gets a power-of-two scale 2^e
 //    with all its entries below 2^(e-1) (A' = [Re A | Im A], B' = [[Re B, Im B],
 //    [-Im B, Re B]] as in the TF32 kernel);
-//  * each real entry x becomes X = rint(x 2^(56-e)) (|X| <= 2^55) and is cut into
-//    balanced base-2^7 digits d1..d8 with |d| <= 64: X = sum d_s 2^(7(8-s)), all
-//    exact in BF16;
-//  * the slice products A_s B_t with s + t = d <= 9 (36 pairs) are summed into one
-//    FP32 accumulator per d (8 accumulators in TMEM).  With K = 2n real terms the
-//    largest group sum is 8 * 64 * 64 * 2n < 2^24 for n <= 256: exact;
-//  * the epilogue forms sum_d G_d 2^(7(9-d)) as two exact int64 halves, rebuilds
-//    each double with integer operations, scaled by 2^(e_A + e_B - 63), and adds them
-//    (GB300's FP64 pipe is narrow: the recombination stays in the integer units).
-// The error is ~2^-55 of |row of A| |column of B| (truncation of the digits and of
-// the pairs with s + t > 9): FP64-class for the RGF tolerances.  (Rows and columns
-// keep their own scales; entries far below their row's or column's largest entry
-// keep an absolute, not a relative, accuracy.)
+//  * each real entry x becomes X = rint(x 2^(7 NS - e)) (|X| <= 2^(7 NS - 1)) and is
+//    cut into balanced base-2^7 digits d1..dNS with |d| <= 64:
+//    X = sum d_s 2^(7(NS-s)), all exact in BF16;
+//  * the slice products A_s B_t with s + t = d <= NS + 1 (NS (NS + 1) / 2 pairs: 36
+//    for NS = 8) are summed into one FP32 accumulator per d (NS accumulators in TMEM).
+//    With K = 2n real terms the largest group sum is NS * 64 * 64 * 2n < 2^24 for
+//    n <= 256: exact;
+//  * the epilogue forms sum_d G_d 2^(7(NS+1-d)) as two exact int64 halves, rebuilds
+//    each double with integer operations, scaled by 2^(e_A + e_B - 7 (NS + 1)), and
+//    adds them (GB300's FP64 pipe is narrow: the recombination stays in the integer
+//    units).
+// The error is ~2^(1 - 7 NS) of |row of A| |column of B| (truncation of the digits and
+// of the pairs with s + t > NS + 1; 2^-55 for NS = 8): FP64-class for the RGF
+// tolerances.  (Rows and columns keep their own scales; entries far below their
+// row's or column's largest entry keep an absolute, not a relative, accuracy.)
 //
 // Tile: 128 rows x 32 complex columns (N = 64 real: 32 real parts, 32 imaginary
-// parts; 8 accumulators x 64 columns fill the 512 TMEM columns), K chunks of 16
+// parts; NS accumulators x 64 columns in a 512-column TMEM allocation), K chunks of 16
 // complex (32 real = 64-byte rows, 64B swizzle), two shared-memory stages.
 #include <stdlib.h>
 
@@ -41,15 +44,19 @@ constexpr int TM = 128;                 // rows per tile
 constexpr int TNC = 32;                 // complex columns per tile
 constexpr int NR = 2 * TNC;             // real MMA columns (64)
 constexpr int KC = 16;                  // complex K per chunk
-constexpr int NS = 8;                   // digits per value
-constexpr int NG = 8;                   // scale groups d = 2..9
+#ifndef NEGF_OZ_DIGITS
+#define NEGF_OZ_DIGITS 8
+#endif
+constexpr int NS = NEGF_OZ_DIGITS;      // digits per value
+constexpr int NG = NS;                  // scale groups d = 2..NS+1
 constexpr int HSPLIT = 4;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
+static_assert(NS >= 6 && NS <= 8, "6 to 8 digits: the group sums and the halves stay exact");
 constexpr int NT = 256;
 constexpr int kCluster = 4;            // column tiles sharing one A tile's digits
 constexpr uint32_t ROWB = 64;                            // bytes per smem row (32 bf16)
 constexpr uint32_t A_SLICE = TM * ROWB;                  // 8 KB
 constexpr uint32_t B_SLICE = NR * ROWB;                  // 4 KB
-constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);     // 96 KB
+constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);     // 96 KB for NS = 8
 constexpr uint32_t SMEM_BYTES = 2 * STAGE + 1024 + 64;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s
 
@@ -210,7 +217,13 @@ __device__ __forceinline__ int scale_exp(double v) {
   return e + 1;
 }
 
-// digits of x at scale 2^e (|x| < 2^(e-1)): X = rint(|x| 2^(7 NS - e)) <= 2^55 is cut
+// sum of 64 in each of the NS - 1 low 7-bit fields (the balancing constant below)
+__host__ __device__ constexpr unsigned long long balance_constant(int fields) {
+  return fields == 0 ? 0ull : (64ull << (7 * (fields - 1))) + balance_constant(fields - 1);
+}
+constexpr unsigned long long kBalance = balance_constant(NS - 1);
+
+// digits of x at scale 2^e (|x| < 2^(e-1)): X = rint(|x| 2^(7 NS - e)) <= 2^(7 NS - 1) is cut
 // into balanced base-2^7 digits (|d| <= 64), d[0] the most significant, and the sign of
 // x is applied to every digit.  Adding 64 to each of the NS - 1 low fields lets binary
 // carries do the balancing: field k of Y = X + 64 sum_k 2^(7k) is f_k + c_(k-1) + 64
@@ -226,8 +239,7 @@ __device__ __forceinline__ void digits(double x, int e, int d[NS]) {
     if (rs <= 0) X = mant << (-rs);
     else if (rs < 64) X = (mant + (1ull << (rs - 1))) >> rs;
   }
-  static_assert(NS == 8, "the balancing constant holds 64 in each of seven 7-bit fields");
-  const unsigned long long Y = X + 0x0001020408102040ull;
+  const unsigned long long Y = X + kBalance;
   const unsigned int lo = (unsigned int)Y, hi = (unsigned int)(Y >> 32);
 #pragma unroll
   for (int k = 0; k < NS - 1; ++k) {
@@ -252,17 +264,27 @@ __device__ __forceinline__ unsigned int bf16_of_int(int v) {
   return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f) >> 16;
 }
 
-static_assert(NG == 8 && HSPLIT == 4, "halves() pairs the eight groups as 2 x 2 x 2");
-// group sums G_0..G_7 of one element (exact FP32 integers) -> the two int64 halves
-// h = sum_{d<4} G_d 2^(7(3-d)), l = sum_{d>=4} G_d 2^(7(7-d)), pairs first in 64-bit IMAD
-__device__ __forceinline__ void halves(const uint32_t (&v)[NG][8], int j, long long& h, long long& l) {
-  long long q[NG / 2];
-#pragma unroll
-  for (int k = 0; k < NG / 2; ++k)
-    q[k] = (long long)__float2int_rn(__uint_as_float(v[2 * k][j])) * 128 +
-           (long long)__float2int_rn(__uint_as_float(v[2 * k + 1][j]));
-  h = q[0] * (1ll << 14) + q[1];
-  l = q[2] * (1ll << 14) + q[3];
+// group pair k of one element: G_2k 2^7 + G_2k+1, or G_2k alone past the last group
+// (the last pair of an odd group count), 0 beyond
+template <int W>
+__device__ __forceinline__ long long group_pair(const uint32_t (&v)[NG][W], int k, int j) {
+  const long long g0 = (2 * k < NG) ? (long long)__float2int_rn(__uint_as_float(v[(2 * k < NG) ? 2 * k : 0][j])) : 0;
+  if (2 * k + 1 >= NG) return g0;
+  return g0 * 128 + (long long)__float2int_rn(__uint_as_float(v[2 * k + 1][j]));
+}
+// the two exact int64 halves of the four group pairs q0..q3:
+// h = sum_{d<4} G_d 2^(7(3-d)) and l = sum_{4<=d<NG} G_d 2^(7(NG-1-d))
+__device__ __forceinline__ void halves_of_pairs(long long q0, long long q1, long long q2, long long q3, long long& h,
+                                                long long& l) {
+  h = q0 * (1ll << 14) + q1;
+  l = (NG == 8) ? q2 * (1ll << 14) + q3 : (NG == 7) ? q2 * (1ll << 7) + q3 : q2;
+}
+static_assert(HSPLIT == 4, "the halves split the groups as [0, 4) and [4, NG)");
+// group sums G_0..G_(NG-1) of one element (exact FP32 integers) -> the two int64 halves
+template <int W>
+__device__ __forceinline__ void halves(const uint32_t (&v)[NG][W], int j, long long& h, long long& l) {
+  halves_of_pairs(group_pair<W>(v, 0, j), group_pair<W>(v, 1, j), group_pair<W>(v, 2, j), group_pair<W>(v, 3, j), h,
+                  l);
 }
 
 // exact int64 (|v| < 2^53) times 2^p as an IEEE double, built with integer operations
@@ -599,7 +621,7 @@ __global__ void __launch_bounds__(NT + 64, 1) zgemm_oz_kernel(GemmArgs g, const 
 // on the same die together and their copies of the shared image hit the L2),
 // digitizes its own 32 B columns in producer warps, and issues the MMAs from one thread.
 // ===========================================================================
-constexpr uint32_t A_IMG = NS * A_SLICE;   // one chunk of one 128-row A tile (64 KB)
+constexpr uint32_t A_IMG = NS * A_SLICE;   // one chunk of one 128-row A tile (64 KB for NS = 8)
 
 struct OzImages {
   unsigned char* a;   // [unit][tiles_m][nchunks] images of A_IMG bytes
@@ -901,8 +923,8 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
 
 // ===========================================================================
 // Half-width tiles, two CTAs per SM.  The same scheme on 128 x 16-complex tiles with
-// K chunks of 8 complex (32-byte rows, 32-byte swizzle): 8 accumulator groups x 32
-// columns = 256 TMEM columns and two 40 KB stages per CTA, so that two CTAs share an
+// K chunks of 8 complex (32-byte rows, 32-byte swizzle): NS accumulator groups x 32
+// columns in 256 TMEM columns and two 40 KB stages per CTA (NS = 8), so that two CTAs share an
 // SM and one's epilogue (integer recombination, issue-bound) overlaps the other's
 // MMAs.  Every CTA copies the A digit image of its row tile into its own shared memory;
 // the column tiles of a row tile run as one cluster (resident on one die together, so
@@ -914,7 +936,7 @@ constexpr int KC2 = 8;                                // complex K per chunk
 constexpr uint32_t ROWB2 = 32;                        // bytes per smem row (16 bf16)
 constexpr uint32_t A_SLICE2 = TM * ROWB2;             // 4 KB
 constexpr uint32_t B_SLICE2 = NR2 * ROWB2;            // 1 KB
-constexpr uint32_t A_IMG2 = NS * A_SLICE2;            // 32 KB: one chunk of one A row tile
+constexpr uint32_t A_IMG2 = NS * A_SLICE2;            // 32 KB (NS = 8): one chunk of one A row tile
 constexpr uint32_t STAGE2 = A_IMG2 + NS * B_SLICE2;   // 40 KB
 constexpr uint32_t SMEM2 = 2 * STAGE2 + 1024 + 64;
 constexpr int NT2 = 192;                              // warps 0-3 B digits + epilogue, 4 copies, 5 MMAs
@@ -1098,7 +1120,7 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
       }
     }
   } else if (warp == 5) {
-    // ---------------- MMA issue: 36 slice pairs (s + t <= NS + 1), one K step per chunk
+    // ---------------- MMA issue: NS (NS + 1) / 2 slice pairs (s + t <= NS + 1), one K step per chunk
     if (lane == 0) {
       for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
@@ -1222,18 +1244,18 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
 // cluster, resident on one die, each copying the unit's whole A image into its own
 // shared memory, so that all but the first read of an image hit the L2), and these
 // groups walk the units in turn.  Full-width tiles (128 x 32 complex, N = 64 per MMA, 512 TMEM
-// columns), K chunks of 8 complex (32-byte rows, 32-byte swizzle, two 48 KB stages;
+// columns), K chunks of 8 complex (32-byte rows, 32-byte swizzle, two 48 KB stages for NS = 8;
 // the A digit images are those of the half-width kernel).  After a tile's MMAs the
 // epilogue warps drain TMEM into a shared-memory buffer of exact int32 group pairs
-// G_2k 2^7 + G_2k+1 (each group sum stays below 2^23 for n <= 128, so a pair stays
-// below 2^31), free TMEM for the next tile, and then recombine the pairs and store D
+// G_2k 2^7 + G_2k+1 (each group sum stays below NS 2^20 < 2^23 for n <= 128, so a pair
+// stays below 2^31), free TMEM for the next tile, and then recombine the pairs and store D
 // while the next tile's MMAs run.
 // Warps 0-7: epilogue (TMEM lanes 32*(w%4), 16 columns each); 8-11 and 12-15: B digits
 // of the stages of even and odd chunk counts; 16: A copies; 17: MMA issue.
 // ===========================================================================
 constexpr int KCP = 8;                                  // complex K per chunk
 constexpr uint32_t B_SLICE_P = NR * ROWB2;              // 2 KB: 64 B'^T rows of 32 bytes
-constexpr uint32_t STAGE_P = A_IMG2 + NS * B_SLICE_P;   // 48 KB
+constexpr uint32_t STAGE_P = A_IMG2 + NS * B_SLICE_P;   // 48 KB for NS = 8
 constexpr uint32_t PAIR_BYTES = TM * TNC * 2 * 16;      // 128 KB: 4 int32 per element and part
 constexpr uint32_t SMEM_P = 2 * STAGE_P + PAIR_BYTES + 1024 + 128;
 constexpr int NT_P = 18 * 32;
@@ -1446,8 +1468,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
           for (int j = 0; j < 4; ++j) {
             int q[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              q[k] = __float2int_rn(__uint_as_float(v[2 * k][j])) * 128 + __float2int_rn(__uint_as_float(v[2 * k + 1][j]));
+            for (int k = 0; k < 4; ++k) q[k] = (int)group_pair<4>(v, k, j);
             pairs[(part * TNC + cbase + 4 * cc + j) * TM + rl] = make_int4(q[0], q[1], q[2], q[3]);
           }
         }
@@ -1481,8 +1502,9 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
             const int col = c0 + j, gcol = n0 + col;
             if (gcol >= n) continue;
             const int4 qr = pairs[col * TM + rl], qi = pairs[(TNC + col) * TM + rl];
-            const long long hr = (long long)qr.x * (1ll << 14) + qr.y, lr = (long long)qr.z * (1ll << 14) + qr.w;
-            const long long hi = (long long)qi.x * (1ll << 14) + qi.y, li = (long long)qi.z * (1ll << 14) + qi.w;
+            long long hr, lr, hi, li;
+            halves_of_pairs(qr.x, qr.y, qr.z, qr.w, hr, lr);
+            halves_of_pairs(qi.x, qi.y, qi.z, qi.w, hi, li);
             const int p = er + ebv[j];
             const int ph = p + 7 * (NG - HSPLIT);
             const zc acc = zmake(ldexp_int(hr, ph) + ldexp_int(lr, p), ldexp_int(hi, ph) + ldexp_int(li, p));
@@ -1510,7 +1532,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
 
 }  // namespace
 
-// exact group sums need NS * 64 * 64 * 2K <= 2^24 per accumulation: the in-kernel-digit
+// exact group sums need NS * 64 * 64 * 2K <= 2^24 per accumulation (K <= 256 for NS <= 8): the in-kernel-digit
 // kernel accumulates the whole K (n <= 256); the digitize-once kernels run K in passes
 bool oz_supported(int n) { return n >= 16 && n <= 512; }
 bool oz_inkernel_supported(int n) { return n >= 16 && n <= 256; }
@@ -1749,3 +1771,5 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
 }
 
 }  // namespace negf
+
+extern "C" int32_t negf_sliced_digits(void) { return negf::NS; }

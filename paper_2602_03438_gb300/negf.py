@@ -29,11 +29,12 @@ MIXED = 1
 MIXED_TF32 = 2
 
 EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
-           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_rgf_keldysh", "negf_observables",
+           "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_rgf_keldysh", "negf_rgf_partitioned",
+           "negf_observables",
            "negf_profile_enable",
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
            "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
-           "negf_mlp_forward", "negf_mlp_train_step"]
+           "negf_mlp_forward", "negf_mlp_train_step", "negf_sliced_digits"]
 KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
 
 
@@ -91,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                       vp, vp, vp, vp, vp]
     lib.negf_rgf_lesser.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                     vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_rgf_partitioned.argtypes = [vp, C.POINTER(_System), C.c_int, i32, vp, vp, C.POINTER(_Scattering),
+                                         vp, vp, vp, vp, vp]
     lib.negf_rgf_keldysh.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_observables.argtypes = [vp, C.POINTER(_System), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -102,6 +105,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_profile_enable.argtypes = [vp, C.c_int]
     lib.negf_profile_read.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.negf_profile_reset.argtypes = [vp]
+    lib.negf_sliced_digits.argtypes = []
     for name in EXPORTS:
         if name not in ("negf_last_error", "negf_mlp_workspace_bytes"):
             getattr(lib, name).restype = C.c_int
@@ -309,6 +313,15 @@ def negf_rgf_lesser(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R,
                                       _stream(stream)))
 
 
+def negf_rgf_partitioned(ctx: Context, sys: System, prec, P: int, sigma_L, sigma_R, scat=None, GR_diag=None,
+                         GR_up=None, GR_low=None, status=None, stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_partitioned(ctx.h, C.byref(s), int(prec), int(P), _ptr(sigma_L), _ptr(sigma_R),
+                                           C.byref(sc) if sc is not None else None, _ptr(GR_diag), _ptr(GR_up),
+                                           _ptr(GR_low), _ptr(status), _stream(stream)))
+
+
 def negf_rgf_keldysh(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, scat=None, GR_diag=None,
                      GR_up=None, GR_low=None, GL_diag=None, GL_low=None, GG_diag=None, GG_low=None, status=None,
                      stream=None):
@@ -376,6 +389,11 @@ def negf_block_inverse(ctx: Context, prec, M, X, status=None, stream=None):
     units = M.shape[0] if M.dim() == 3 else 1
     ctx.check(ctx.lib.negf_block_inverse(ctx.h, int(prec), n, units, _ptr(M), _ptr(X), _ptr(status),
                                          _stream(stream)))
+
+
+def sliced_digits() -> int:
+    """Digits per value of the NEGF_MIXED sliced product in the loaded build."""
+    return int(load_library().negf_sliced_digits())
 
 
 def negf_block_gemm_noalloc(A, B, D, opA=0, opB=0, alpha=1.0, beta=0.0, C_=None, status=None, stream=None):

@@ -80,13 +80,23 @@ def test_roofline_arithmetic():
     assert r2["bound"] == "alu" and r2["peak"] == 1.25
 
 
-def test_roofline_sliced_gemm_counts_tensor_work():
+def test_roofline_sliced_gemm_counts_useful_work_against_tf32_third():
+    """The sliced product's roofline counts the useful 8 n^3 flops of a complex product
+    against the useful peak of a complex product on the tensor cores (TF32 peak / 3,
+    TF32 = bf16 x 1.1/2.25); the executed BF16 work (OZ_SLICE_PAIRS slice pairs per
+    complex product) is reported beside."""
     peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1650.0}
     st = {"launches": 4, "ms": 8.0, "flops": 4 * 8 * 128 ** 3 * 100.0, "bytes": 0.0}
     r = bench.roofline_for("gemm_oz", st, peaks, "measured")
     useful = 8 * 128 ** 3 * 100.0 / 2e-3 / 1e12
     assert abs(r["useful_tflops"] - useful) < 1e-9
-    assert abs(r["achieved"] - 36 * useful) < 1e-9 and r["peak"] == 1650.0
+    assert abs(r["achieved"] - useful) < 1e-9
+    assert abs(r["peak"] - 1650.0 * 1.1 / 2.25 / 3.0) < 1e-9
+    assert abs(r["frac"] - useful / r["peak"]) < 1e-12
+    pairs = bench.OZ_SLICE_PAIRS
+    assert pairs == 36.0   # 8 digits, s + t <= 9 (the library default)
+    assert abs(r["executed_bf16_tflops"] - pairs * useful) < 1e-9
+    assert abs(r["executed_bf16_frac"] - pairs * useful / 1650.0) < 1e-12
 
 
 def test_traffic_record_matches_the_kernel_source(tmp_path, monkeypatch):
