@@ -37,6 +37,7 @@ __all__ = [
     "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
     "interface_current", "density", "solve_energy", "retarded_check", "surface_newton_warm",
     "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf", "partitioned_retarded",
+    "energy_convolution", "scba_self_energies", "scba_loop",
 ]
 
 
@@ -596,6 +597,74 @@ def partitioned_retarded(dev, z, sigma_L, sigma_R, P, sigR_scat=None):
     return dict(GR_diag=np.stack(GRd),
                 GR_up=np.stack(GRu) if nb > 1 else np.zeros((0, b, b), complex),
                 GR_low=np.stack(GRl) if nb > 1 else np.zeros((0, b, b), complex))
+
+
+# ---------------------------------------------------------------------------
+# Eq. (3): energy convolution and the self-consistent scattering loop (Fig. 2)
+# ---------------------------------------------------------------------------
+
+def energy_convolution(X, w):
+    """Eq. (3) on a uniform energy grid with a scalar kernel: Y[n] = sum_m w[m] X[n - m]
+    for m = -M..M (w has 2M+1 entries, w[0] is m = -M), X taken as zero outside the grid.
+    X has the energy as its first axis; the sum runs element by element over the rest."""
+    X = np.asarray(X)
+    ne = X.shape[0]
+    M = (len(w) - 1) // 2
+    Y = np.zeros_like(X)
+    for n in range(ne):
+        for j, m in enumerate(range(-M, M + 1)):
+            k = n - m
+            if 0 <= k < ne and w[j] != 0.0:
+                Y[n] = Y[n] + w[j] * X[k]
+    return Y
+
+
+def scba_self_energies(GL_diag, GG_diag, w_less, w_great):
+    """Scattering self-energies of the self-consistent loop from the diagonal blocks of
+    G^< and G^> over all energies ([ne][nb][b][b]): Sigma^<(E) = sum_m w^<_m G^<(E - w_m),
+    Sigma^>(E) = sum_m w^>_m G^>(E - w_m) (Eq. (3), C1 = G, C2 = the scalar kernel), and
+    Sigma^R = (Sigma^> - Sigma^<) / 2 (the anti-Hermitian part; the principal-value part
+    is not kept)."""
+    SL = energy_convolution(GL_diag, w_less)
+    SG = energy_convolution(GG_diag, w_great)
+    return 0.5 * (SG - SL), SL, SG
+
+
+def scba_loop(dev, w_less, w_great, sigma=None, mixing=0.5, tol=1e-8, max_iter=100):
+    """The self-consistent scattering loop of Fig. 2 for block-diagonal scattering:
+    start from Sigma^{R,<,>} = 0; at every step solve Eq. (1)-(2) for G^R, G^<, G^> at all
+    energies (block recursion), form the new self-energies by Eq. (3), and mix
+    Sigma <- (1 - mixing) Sigma + mixing Sigma_new (for Sigma^< and Sigma^>, Sigma^R
+    following from them); stop when max|Sigma^<_new - Sigma^<|, max|Sigma^>_new - Sigma^>|
+    are both below tol times the largest entry of the new ones.  `sigma` = (Sigma_L,
+    Sigma_R) per energy, else the decimation gives them.  Returns the self-energies, the
+    last Green's functions, the step count and the last change."""
+    ne, nb, b = dev.ne, dev.nb, dev.b
+    if sigma is None:
+        sig = [lead_self_energies(dev, dev.energy[e] + 1j * dev.eta)[:2] for e in range(ne)]
+    else:
+        sig = [(sigma[0][e], sigma[1][e]) for e in range(ne)]
+    fL, fR = dev.f_L(), dev.f_R()
+    SR = np.zeros((ne, nb, b, b), complex)
+    SL = np.zeros_like(SR)
+    SG = np.zeros_like(SR)
+    change, it = np.inf, 0
+    out = None
+    while it < max_iter:
+        it += 1
+        out = [rgf_blocks(dev, dev.energy[e] + 1j * dev.eta, sig[e][0], sig[e][1], fL[e], fR[e],
+                          sigR_scat=SR[e], sigL_scat=SL[e], greater=True) for e in range(ne)]
+        GLd = np.stack([o["GL_diag"] for o in out])
+        GGd = np.stack([o["GG_diag"] for o in out])
+        _, SLn, SGn = scba_self_energies(GLd, GGd, w_less, w_great)
+        scale = max(np.abs(SLn).max(), np.abs(SGn).max(), 1e-300)
+        change = max(np.abs(SLn - SL).max(), np.abs(SGn - SG).max()) / scale
+        SL = (1.0 - mixing) * SL + mixing * SLn
+        SG = (1.0 - mixing) * SG + mixing * SGn
+        SR = 0.5 * (SG - SL)
+        if change < tol:
+            break
+    return dict(sigR=SR, sigL=SL, sigG=SG, out=out, iters=it, change=change)
 
 
 # ---------------------------------------------------------------------------

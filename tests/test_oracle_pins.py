@@ -455,3 +455,70 @@ def test_partitioned_retarded_rejects_uneven_partitions():
         O.partitioned_retarded(dev, z, np.zeros((4, 4)), np.zeros((4, 4)), 2)
     with pytest.raises(ValueError):
         O.partitioned_retarded(dev.truncated(nb=4), z, np.zeros((4, 4)), np.zeros((4, 4)), 4)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (3) energy convolution and the self-consistent scattering loop (Fig. 2)
+# ---------------------------------------------------------------------------
+
+def test_energy_convolution_is_a_shift_for_a_delta_kernel():
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(40, 3, 2)) + 1j * rng.normal(size=(40, 3, 2))
+    for M, k in ((3, 2), (3, -3), (5, 0)):
+        w = np.zeros(2 * M + 1)
+        w[k + M] = 1.5
+        Y = O.energy_convolution(X, w)
+        for n in range(40):
+            ref = 1.5 * X[n - k] if 0 <= n - k < 40 else 0.0
+            assert np.all(Y[n] == ref), (M, k, n)
+
+
+def test_energy_convolution_matches_numpy_convolve_on_scalars():
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=57) + 1j * rng.normal(size=57)
+    w = rng.uniform(0, 1, size=9)
+    full = np.convolve(x, w)            # full[i] = sum_j w[j] x[i - j]
+    y = O.energy_convolution(x[:, None], w)[:, 0]
+    assert np.abs(y - full[4:4 + 57]).max() <= 1e-13 * np.abs(full).max()
+
+
+def _scba_setup(eta=None, g2=0.05):
+    dev = W.scba_device(6, 8, 128)
+    if eta is not None:
+        dev.eta = eta
+    wl, wg = W.einstein_kernel(dev.energy, 4, g2, dev.kT)
+    return dev, wl, wg
+
+
+def test_scba_without_coupling_is_the_ballistic_solution():
+    dev, wl, wg = _scba_setup(g2=0.0)
+    dev = dev.truncated(energies=np.arange(0, 128, 16))
+    r = O.scba_loop(dev, wl, wg)
+    assert r["iters"] == 1 and np.all(r["sigL"] == 0)
+    for e in range(dev.ne):
+        ref = O.solve_energy(dev, e, use_rgf=True)
+        assert np.abs(r["out"][e]["GL_diag"] - ref["GL_diag"]).max() <= 1e-13 * np.abs(ref["GL_diag"]).max()
+
+
+def test_scba_converges_to_a_fixed_point_that_conserves_the_integrated_current():
+    """At the fixed point the scattering only moves electrons between energies: the
+    energy-resolved current J_i(E) changes along the device, the energy-integrated one
+    does not (the scattering sources cancel over the grid because w^>_m = w^<_-m).  The
+    broadening eta is an additional sink of 2 eta x (electrons per block), so the
+    check runs at eta = 1e-10."""
+    dev, wl, wg = _scba_setup(eta=1e-10)
+    r = O.scba_loop(dev, wl, wg, mixing=0.5, tol=1e-9, max_iter=80)
+    assert r["change"] < 1e-9
+    # fixed point: the self-energies of the final Green's functions are the mixed ones
+    GLd = np.stack([o["GL_diag"] for o in r["out"]])
+    GGd = np.stack([o["GG_diag"] for o in r["out"]])
+    SR, SL, SG = O.scba_self_energies(GLd, GGd, wl, wg)
+    scale = np.abs(SG).max()
+    assert np.abs(SL - r["sigL"]).max() <= 1e-8 * scale
+    assert np.abs(SG - r["sigG"]).max() <= 1e-8 * scale
+    assert np.abs(SR + H(SR)).max() <= 1e-10 * scale        # anti-Hermitian Sigma^R (to rounding)
+    J = np.stack([O.interface_current(dev, dev.energy[e] + 1j * dev.eta, r["out"][e]["GL_low"])
+                  for e in range(dev.ne)])
+    Jint = J.sum(axis=0)
+    assert np.ptp(Jint) <= 1e-6 * np.abs(Jint).max()
+    assert np.abs(np.ptp(J, axis=1)).max() >= 1e-2 * np.abs(J).max()

@@ -296,3 +296,37 @@ def ideal_multiorbital(nb: int, H00: np.ndarray, H01: np.ndarray, energy, eta: f
     Hd = np.broadcast_to(H00, (nb, b, b)).astype(np.complex128).copy()
     Hu = np.broadcast_to(H01, (max(nb - 1, 0), b, b)).astype(np.complex128).copy()
     return Device(Hd, Hu, None, None, np.asarray(energy, dtype=np.float64), eta, name="ideal")
+
+
+# --------------------------------------------------------------------------
+# self-consistent scattering (Fig. 2 loop): a device that carries current, and the
+# phonon-like scalar kernel of the energy convolution of Eq. (3)
+# --------------------------------------------------------------------------
+
+def scba_device(nb: int = 8, b: int = 16, ne: int = 256, seed: int = SEED_BASE + 6,
+                e_min: float = -4.5, e_max: float = 4.5) -> Device:
+    """Config-4 style device for the self-consistent loop, at loop-friendly sizes: the
+    banded generator plus a dense random inter-slice coupling (sigma 0.3 / sqrt(b)) so
+    that current flows, S = I + 0.05 R, mu_L - mu_R = 0.2, kT = 0.025, on a uniform
+    grid wide enough that no spectral weight leaves it when shifted by the kernel."""
+    dev = banded_device(nb, b, ne, seed, overlap=True, e_min=e_min, e_max=e_max, name="scba")
+    rng = _rng(seed + 500)
+    if nb > 1:
+        dev.H_up = dev.H_up + 0.3 * _cn(rng, dev.H_up.shape) / np.sqrt(b)
+    return dev
+
+
+def einstein_kernel(energy: np.ndarray, steps: int, g2: float, kT: float):
+    """Weights of an Einstein boson of energy hw0 = steps * dE (dE the grid step) for the
+    convolution Sigma^x(E) = sum_m w^x_m G^x(E - m dE), m = -steps..steps: absorption
+    (m = +steps) with N, emission (m = -steps) with N + 1 for Sigma^<; the reverse for
+    Sigma^>; N the Bose occupation at kT, g2 the squared coupling.  Returns (w_less,
+    w_great), each of length 2 steps + 1 (entry 0 is m = -steps)."""
+    de = float(energy[1] - energy[0])
+    w0 = steps * de
+    nbose = 1.0 / np.expm1(w0 / kT)
+    wl = np.zeros(2 * steps + 1)
+    wg = np.zeros(2 * steps + 1)
+    wl[2 * steps], wl[0] = g2 * nbose, g2 * (nbose + 1.0)
+    wg[2 * steps], wg[0] = g2 * (nbose + 1.0), g2 * nbose
+    return wl, wg
