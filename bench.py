@@ -608,6 +608,76 @@ def run_probe(args):
     ctx.close()
 
 
+def run_config4(args):
+    """Config 4 at its stated size: nb = 32, b = 512, all 512 energies, block-diagonal
+    scattering.  The Green's function blocks of all energies would take 343 GB, so the
+    sweeps and observables run chunk by chunk in the workspace (negf_rgf_observables):
+    one timed run of OBC + sweeps + T, DOS, current and density over every energy, mixed
+    precision; then the current of `fp64_sample` sampled energies from the FP64 sweeps
+    (blocks stored, same Sigma) against the mixed run's (|dJ| / max(|J|, 1e-3 max|J|))."""
+    import torch
+    import paper_2602_03438_gb300 as P
+    torch.cuda.set_device(0)
+    dev = W.config4()
+    ctx = P.Context(0, int(args.workspace_gb * (1 << 30)))
+    sys_ = P.upload(dev)
+    L = sys_.layout()[-1]
+    cz = lambda n: torch.empty(int(n), dtype=torch.complex128, device="cuda")
+    z64 = lambda n: torch.zeros(int(n), dtype=torch.float64, device="cuda")
+    sig_L, sig_R = cz(L[3]), cz(L[3])
+    st_obc = torch.zeros(dev.ne, dtype=torch.int32, device="cuda")
+    status = torch.zeros(dev.ne, dtype=torch.int32, device="cuda")
+    iters = torch.zeros(2 * dev.ne, dtype=torch.int32, device="cuda")
+    T, dos, J, n = z64(L[2]), z64(L[2]), z64(L[6]), z64(L[7])
+    fL = torch.from_numpy(dev.f_L()).cuda()
+    fR = torch.from_numpy(dev.f_R()).cuda()
+    w = torch.from_numpy(dev.weights()).cuda()
+    sc = P.Scattering.from_devices([dev])
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    P.negf_obc(ctx, sys_, sig_L, sig_R, iters, st_obc, prec=P.MIXED)
+    e1.record()
+    P.negf.negf_rgf_observables(ctx, sys_, P.MIXED, sig_L, sig_R, fL, fR, sc, w, T, dos, J, n, status)
+    e2.record()
+    torch.cuda.synchronize()
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the config-4 run")
+    ms_obc, ms_sw = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    # FP64 sweeps with stored blocks on sampled energies, same Sigma
+    k = max(1, min(args.fp64_sample, dev.ne))
+    idx = np.linspace(0, dev.ne - 1, k).round().astype(int)
+    sub = dev.truncated(energies=idx)
+    s2 = P.upload(sub)
+    o2 = P.allocate_outputs(s2)
+    sel = torch.from_numpy(idx).cuda()
+    bb = dev.b * dev.b
+    o2["sigma_L"].copy_(sig_L.view(dev.ne, bb)[sel].reshape(-1))
+    o2["sigma_R"].copy_(sig_R.view(dev.ne, bb)[sel].reshape(-1))
+    sc2 = P.Scattering.from_devices([sub])
+    f2L, f2R = fL[sel].contiguous(), fR[sel].contiguous()
+    P.negf_rgf_lesser(ctx, s2, P.FP64, o2["sigma_L"], o2["sigma_R"], f2L, f2R, sc2, o2["GR_diag"], o2["GR_up"],
+                      o2["GR_low"], o2["GL_diag"], o2["GL_low"], o2["status"])
+    P.negf_observables(ctx, s2, o2["sigma_L"], None, None, None, None, None, o2["GL_low"], None, None,
+                       o2["current"], None, prec=P.FP64)
+    torch.cuda.synchronize()
+    J64 = o2["current"].cpu().numpy().reshape(k, dev.nb - 1)
+    Jm = J.cpu().numpy().reshape(dev.ne, dev.nb - 1)[idx]
+    floor = 1e-3 * max(np.abs(J64).max(), 1e-300)
+    line = {"workload": "config4", "devices": 1, "energies": dev.ne, "nb": dev.nb, "b": dev.b,
+            "mixed": {"value": dev.ne / ((ms_obc + ms_sw) / 1e3), "unit": UNIT, "ms_per_run": ms_obc + ms_sw,
+                      "ms_obc": ms_obc, "ms_sweeps_and_observables": ms_sw,
+                      "what": "OBC + G^R/G^< sweeps + T, DOS, current, density over all 512 energies, mixed "
+                              "precision, blocks kept in the workspace chunk by chunk (negf_rgf_observables)"},
+            "J_err_vs_fp64": float((np.abs(Jm - J64) / np.maximum(np.abs(J64), floor)).max()),
+            "fp64_sampled_energies": idx.tolist(),
+            "finite": bool(np.isfinite(J.cpu().numpy()).all() and np.isfinite(n.cpu().numpy()).all()),
+            "status": {"obc_not_converged": int((st_obc != 0).sum().item()),
+                       "rgf_flagged": int((status != 0).sum().item())}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_workload(args):
     """Mixed vs FP64 on the other workloads (not the headline line): --workload config4 runs
     the nb = 32, b = 512 device with block-diagonal scattering over `ne` energies;
@@ -630,6 +700,8 @@ def run_workload(args):
             d = W.config3_device(k, shapes)
             devs.append(d.truncated(energies=np.linspace(0, d.ne - 1, min(args.ne_cap, d.ne)).round().astype(int)))
     ctx = P.Context(0, int(args.workspace_gb * (1 << 30)))
+    # tile shapes of the block products: the autotuner's choice per block size
+    tuned = P.tuning.tune(ctx, sorted(set(d.b for d in devs)), units=256)["choices"]
     sys_ = P.upload(devs)
     out = P.allocate_outputs(sys_)
     sc = P.Scattering.from_devices(devs) if devs[0].sigR_scat is not None else None
@@ -639,6 +711,10 @@ def run_workload(args):
 
     def step():
         P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"], prec=P.MIXED)
+        P.negf_rgf_lesser(ctx, sys_, P.MIXED, out["sigma_L"], out["sigma_R"], fL, fR, sc, out["GR_diag"],
+                          out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
+
+    def sweeps():
         P.negf_rgf_lesser(ctx, sys_, P.MIXED, out["sigma_L"], out["sigma_R"], fL, fR, sc, out["GR_diag"],
                           out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
 
@@ -653,6 +729,15 @@ def run_workload(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # the sweeps alone (Sigma_OBC precomputed), with the kernel launch count
+    ctx.profile_reset()
+    e0.record()
+    for _ in range(args.steps):
+        sweeps()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sw = e0.elapsed_time(e1) / args.steps
+    launches_sw = ctx.profile_read()["launches"] / args.steps
     # FP64 sweeps on a sample of each device's energies, given the mixed run's Sigma
     L = sys_.layout()
     subs, idx_all = [], []
@@ -704,8 +789,13 @@ def run_workload(args):
             "block_sizes": sorted(set(d.b for d in devs)),
             "mixed": {"value": ne_tot / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
                       "what": "OBC + G^R/G^< sweeps, mixed precision, every energy"},
+            "mixed_sweeps": {"value": ne_tot / (ms_sw / 1e3), "unit": UNIT, "ms_per_run": ms_sw,
+                             "launches_per_run": launches_sw,
+                             "what": "G^R/G^< sweeps alone (Sigma_OBC precomputed): devices of one block "
+                                     "size sweep together, one launch per step over all their units"},
             "fp64_sweeps": {"value": n64 / (ms64 / 1e3), "unit": UNIT, "energies": n64},
             "err_vs_fp64": err,
+            "tuned_variants": {n: v["variant"] for n, v in tuned.items()},
             "status": {"obc_not_converged": int((out["obc_status"] != 0).sum().item()),
                        "rgf_flagged": int((out["status"] != 0).sum().item())}}
     print(json.dumps(line), flush=True)
@@ -737,6 +827,8 @@ def main(argv=None):
         run_probe_partitioned(args)
     elif args.probe:
         run_probe(args)
+    elif args.workload == "config4":
+        run_config4(args)
     elif args.workload:
         run_workload(args)
     elif args.impl == "reference":

@@ -124,6 +124,19 @@ negf_status negf_ctx_sync(negf_ctx* ctx, negf_stream stream);
  * plus, at out[8*ndev .. 8*ndev+7], the totals.  `out` has 8*(ndev+1) entries. */
 negf_status negf_layout(const negf_system* sys, int64_t* out);
 
+/* Host-only work list of the batched sweeps of an uneven batch (integer work, Sec. II:
+ * every energy of every device is independent).  The devices with block size `bs` and
+ * ne > 0 sweep together when there are two or more of them: one launch per sweep step
+ * over all their (device, energy) units, step i of the forward sweep active for the
+ * units whose device has block i, step i of the backward sweep for those with block
+ * i + 1.  Writes *count = the number of such units and, for each unit u in
+ * device-then-energy order (each array may be NULL): unit_dev[u] (device index),
+ * unit_e[u] (energy index within the device), off_d[u] = [4] + e nb b^2 and
+ * off_o[u] = [5] + e (nb - 1) b^2 of negf_layout (element offsets of the unit's block 0
+ * in the diagonal and the off-diagonal outputs).  Call with NULL arrays to size them. */
+negf_status negf_worklist(const negf_system* sys, int32_t bs, int32_t* count, int32_t* unit_dev, int32_t* unit_e,
+                          int64_t* off_d, int64_t* off_o);
+
 /* Lead self-energies (open boundary term of B^R, Sec. II "LSE+OBC").
  * The left lead repeats block 0 with hop H_{0,1} (S likewise); the right lead
  * repeats block nb-1 with hop H_{nb-2,nb-1}.  Surface Green's functions by
@@ -202,6 +215,27 @@ negf_status negf_rgf_partitioned(negf_ctx* ctx, const negf_system* sys, negf_pre
                                  void* GR_diag, void* GR_up, void* GR_low, int32_t* status,
                                  negf_stream stream);
 
+/* Selected inversion of the arrowhead BT (BTA) matrix (the block-tridiagonal-arrowhead
+ * shape of the Serinv solver the paper uses): the device's A(z) of negf_rgf_retarded
+ * bordered by one tip block t of size b (a gate), with overlap I on the tip and none on
+ * the arrow:
+ *     A_tt = z I - H_tip,   A_(t,i) = -H_(t,i),   A_(i,t) = -H_(t,i)^H,   i = 0..nb-1.
+ * Every device block is eliminated downward with the tip as the boundary they all couple
+ * to; the tip's Schur complement is inverted last and the blocks are rebuilt from it.
+ * Work per block: 14 block products and 1 inverse (120 b^3 real flops, against 56 b^3
+ * for the BT recursion).
+ *   H_tip   : in, device [sum b*b]: one tip Hamiltonian per device (device after device).
+ *   H_arrow : in, device [sum nb] blocks H_(t,i) (the layout of H_diag).
+ *   GR_diag, GR_up, GR_low : out, the device's selected blocks of G^R (up/low required
+ *             when nb > 1).
+ *   G_tip   : out, device [sum ne] blocks G_tt (the layout of sigma_L).
+ *   G_row, G_col : out, device [sum ne*nb] blocks G_(t,i) and G_(i,t) (the layout of GR_diag).
+ * Other arguments as negf_rgf_retarded. */
+negf_status negf_rgf_arrowhead(negf_ctx* ctx, const negf_system* sys, negf_precision prec, const void* H_tip,
+                               const void* H_arrow, const void* sigma_L, const void* sigma_R,
+                               const negf_scattering* scat, void* GR_diag, void* GR_up, void* GR_low,
+                               void* G_tip, void* G_row, void* G_col, int32_t* status, negf_stream stream);
+
 /* G^R, G^< and G^> (Eq. (2) for both B^<, B^>) in one fused sweep pair: the retarded
  * sweep once, then the lesser recursion of negf_rgf_lesser run twice, on Sigma^< and on
  *     Sigma^> = Sigma^>_scat - i (1 - f_L) Gamma_L - i (1 - f_R) Gamma_R,
@@ -219,6 +253,64 @@ negf_status negf_rgf_keldysh(negf_ctx* ctx, const negf_system* sys, negf_precisi
                              void* GR_diag, void* GR_up, void* GR_low,
                              void* GL_diag, void* GL_low, void* GG_diag, void* GG_low,
                              int32_t* status, negf_stream stream);
+
+/* Eq. (3) on a uniform energy grid with a scalar kernel (M_1 = M_2 = I, C_2 a scalar
+ * function of the energy transfer):
+ *     Y[e][i] = sum_{m=-M..M} w[m+M] X[e-m][i],   i < nelem, X = 0 outside 0 <= e < ne,
+ * for complex128 X, Y (device) with element i of energy e at X + e*ld + i (ld >= nelem).
+ * w: host [2M+1].  Evaluated as a zero-padded circular convolution by FFT of size
+ * N = 2^k >= ne + M (Sec. II: the energy convolution in the time domain after an FFT),
+ * FP64; ne + M <= 8192 (else NEGF_ERR_ARG).  X and Y must not overlap. */
+negf_status negf_energy_convolution(negf_ctx* ctx, int32_t ne, int64_t nelem, int64_t ld, int32_t M,
+                                    const double* w, const void* X, void* Y, negf_stream stream);
+
+/* Scalar boson kernel of the scattering self-energies (the C_2 of Eq. (3)). */
+typedef struct {
+  int32_t M;                 /* support: energy transfers m dE, m = -M..M (dE: the grid step) */
+  const double* w_lesser;    /* host [2M+1]: Sigma^<(E) += w_lesser[m+M] G^<(E - m dE)       */
+  const double* w_greater;   /* host [2M+1]: Sigma^>(E) += w_greater[m+M] G^>(E - m dE)      */
+} negf_boson_kernel;
+
+/* The self-consistent scattering loop of Fig. 2 (the Born approximation with a scalar
+ * boson kernel), on the diagonal blocks:
+ *   repeat: G^R, G^<, G^> of all energies (negf_rgf_keldysh) with the current
+ *           block-diagonal Sigma^R_scat, Sigma^<_scat (per energy);
+ *           Sigma^x_new(E) = sum_m w^x_m G^x_ii(E - m dE) for x = <, > (Eq. (3), by FFT);
+ *           change = max(max|Sigma^<_new - Sigma^<|, max|Sigma^>_new - Sigma^>|)
+ *                    / max(|Sigma^<_new|, |Sigma^>_new|);
+ *           Sigma^x += mixing (Sigma^x_new - Sigma^x);  Sigma^R = (Sigma^> - Sigma^<) / 2
+ *           (the anti-Hermitian part; no principal-value part);
+ *   until change < tol or max_iter sweeps.
+ * Every device's energies must be a uniform grid whose step dE is the kernel's; the
+ * returned G blocks are those of the last sweep (made with the Sigma before its update).
+ *   sigR_scat, sigL_scat, sigG_scat: in/out, device [sum ne*nb] blocks (energy-major,
+ *     the per_energy layout of negf_scattering): start values (zero for a cold start),
+ *     then the mixed self-energies.
+ *   GR_diag, GL_diag, GG_diag required; GR_up, GR_low, GL_low, GG_low may be NULL.
+ *   iters, change: host out (sweeps done, last change), each may be NULL.
+ * The workspace must also hold 2 [sum ne*nb] blocks for the new self-energies (else
+ * NEGF_ERR_NOMEM).  The host reads the change after every sweep (one synchronization
+ * per sweep). */
+negf_status negf_scba(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
+                      const void* sigma_L, const void* sigma_R, const double* f_L, const double* f_R,
+                      const negf_boson_kernel* kern, double mixing, double tol, int32_t max_iter,
+                      void* sigR_scat, void* sigL_scat, void* sigG_scat,
+                      void* GR_diag, void* GR_up, void* GR_low, void* GL_diag, void* GL_low,
+                      void* GG_diag, void* GG_low, int32_t* status, int32_t* iters, double* change,
+                      negf_stream stream);
+
+/* The sweeps and the observables of every energy without storing any Green's function
+ * block for the caller: energies are processed in chunks that fit the workspace, each
+ * chunk's G^R and G^< blocks kept there only until its observables (as negf_observables)
+ * are taken.  For batches whose blocks do not fit the GPU's memory (a b = 512, nb = 32
+ * device needs 628 MB of blocks per energy).  Arguments as negf_rgf_lesser and
+ * negf_observables (prec applies to both); T, dos, current, density may each be NULL;
+ * density accumulates over all chunks with the weights e_weight. */
+negf_status negf_rgf_observables(negf_ctx* ctx, const negf_system* sys, negf_precision prec,
+                                 const void* sigma_L, const void* sigma_R, const double* f_L, const double* f_R,
+                                 const negf_scattering* scat, const double* e_weight,
+                                 double* T, double* dos, double* current, double* density,
+                                 int32_t* status, negf_stream stream);
 
 /* Observables (Sec. III: DOS, spectral current, current conservation), traces and sums
  * in FP64.  prec: the two block products of T (Gamma_L G_00 and G_00 Gamma_L) run in FP64
@@ -293,6 +385,23 @@ negf_status negf_block_gemm_noalloc(int32_t n, int32_t units, int32_t opA, int32
                                     const void* A, int64_t a_stride, const void* B, int64_t b_stride,
                                     const double* beta, const void* C, int64_t c_stride, void* D,
                                     int64_t d_stride, int32_t* status, negf_stream stream);
+
+/* Autotuner of the NEGF_MIXED block products' tile shapes.  Variants:
+ *   1 = half-width tiles (128 rows x 16 complex columns, two CTAs per SM; n <= 128),
+ *   2 = persistent full-width tiles (128 x 32, the epilogue of one unit overlapping the
+ *       next unit's MMAs; n <= 128),
+ *   3 = full-width tiles, one CTA per tile (any n, K in exact passes of 256),
+ *   0 = the built-in rule (1 for n <= 96, 2 for n <= 128, 3 above).
+ * negf_tune_products times every variant that supports n on `units` random n x n
+ * products in the context's workspace (1 warm-up + 3 calls each, CUDA events on
+ * `stream`), makes the fastest the context's choice for n and returns it in *choice
+ * (0 when no sliced product exists for n); ms (host [4] or NULL) gets each variant's
+ * time per call (-1 where not timed).  It synchronizes the stream.  NEGF_ERR_NOMEM if
+ * the workspace cannot hold 3 units x n^2 blocks and the product's scratch.
+ * negf_set_product_variant sets the choice for n directly (e.g. from a saved tuning). */
+negf_status negf_tune_products(negf_ctx* ctx, int32_t n, int32_t units, int32_t* choice, double* ms,
+                               negf_stream stream);
+negf_status negf_set_product_variant(negf_ctx* ctx, int32_t n, int32_t variant);
 
 /* Digits per value of the NEGF_MIXED sliced product in this build (NEGF_OZ_DIGITS at
  * compile time, 6..8; 8 by default): NS digits of 7 bits give an error of ~2^(1 - 7 NS)

@@ -37,7 +37,7 @@ __all__ = [
     "greens_dense", "rgf_blocks", "transmission_caroli", "transmission_g00", "dos",
     "interface_current", "density", "solve_energy", "retarded_check", "surface_newton_warm",
     "warm_surface_gf", "stein_smith", "surface_newton", "surface_gf", "partitioned_retarded",
-    "energy_convolution", "scba_self_energies", "scba_loop",
+    "energy_convolution", "scba_self_energies", "scba_loop", "arrowhead_dense",
 ]
 
 
@@ -597,6 +597,36 @@ def partitioned_retarded(dev, z, sigma_L, sigma_R, P, sigR_scat=None):
     return dict(GR_diag=np.stack(GRd),
                 GR_up=np.stack(GRu) if nb > 1 else np.zeros((0, b, b), complex),
                 GR_low=np.stack(GRl) if nb > 1 else np.zeros((0, b, b), complex))
+
+
+# ---------------------------------------------------------------------------
+# arrowhead BT matrices: a dense border block (a gate) coupled to every block
+# ---------------------------------------------------------------------------
+
+def arrowhead_dense(dev, z, sigma_L, sigma_R, H_tip, H_arrow, sigR_scat=None):
+    """Eq. (1) for the block-tridiagonal-with-arrowhead (BTA) matrix: the device's A(z)
+    bordered by one more block row and column, the tip t (size b, overlap I, Hamiltonian
+    H_tip) coupled to block i by H_(t,i) = H_arrow[i] (overlap 0):
+        A_tt = z I - H_tip,   A_(t,i) = -H_arrow[i],   A_(i,t) = -H_arrow[i]^H.
+    Returns the selected blocks of G^R = A^{-1}: GR_diag, GR_up, GR_low of the device, the
+    tip G_tt and the arrow blocks G_(t,i) (row) and G_(i,t) (column)."""
+    b, nb = dev.b, dev.nb
+    A = assemble_A(dev, z, sigma_L, sigma_R, sigR_scat)
+    N = nb * b
+    Ab = np.zeros((N + b, N + b), dtype=np.complex128)
+    Ab[:N, :N] = A
+    Ab[N:, N:] = z * np.eye(b) - H_tip
+    for i in range(nb):
+        Ab[N:, i * b:(i + 1) * b] = -H_arrow[i]
+        Ab[i * b:(i + 1) * b, N:] = -_H(H_arrow[i])
+    G = np.linalg.inv(Ab)
+    return dict(
+        GR_diag=np.stack([_blk(G, i, i, b) for i in range(nb)]),
+        GR_up=np.stack([_blk(G, i, i + 1, b) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, b, b), complex),
+        GR_low=np.stack([_blk(G, i + 1, i, b) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, b, b), complex),
+        G_tip=G[N:, N:].copy(),
+        G_row=np.stack([G[N:, i * b:(i + 1) * b] for i in range(nb)]),
+        G_col=np.stack([G[i * b:(i + 1) * b, N:] for i in range(nb)]))
 
 
 # ---------------------------------------------------------------------------

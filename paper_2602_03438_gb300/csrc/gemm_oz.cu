@@ -632,7 +632,8 @@ struct OzImages {
 };
 
 // A operand: one CTA per (32 rows, unit); each writes its rows of the 128-row tile images
-__global__ void __launch_bounds__(256) oz_digitize_a_kernel(GemmArgs g, OzImages im) {
+template <class ARGS>
+__global__ void __launch_bounds__(256) oz_digitize_a_kernel(ARGS g, OzImages im) {
   const int u = blockIdx.y;
   if (g.active && !g.active[u]) return;
   constexpr int RB = 32;
@@ -960,7 +961,32 @@ __device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
 // column scales of op(B) of unit u for n <= 128, by one CTA of 256 threads: the
 // columns of B (op N, two threads per column over alternate rows) or the rows of B
 // (op H, a warp per row)
-__device__ __forceinline__ void b_col_scales(const GemmArgs& g, int u, int* eb) {
+// the operands of a pre-pass in the plain layout (unit u at p + u us): a compact argument
+// struct, so that the pre-pass compiles as for a strided batch (the general BMat's extra
+// fields in the kernel arguments cost the pre-pass ~20 % of its time)
+struct PlainMat {
+  const zc* p;
+  long long us;
+  __device__ const zc* at(int u) const { return p + (long long)u * us; }
+};
+struct PreArgs {
+  PlainMat A, B;
+  int opA, opB, n;
+  const int* active;
+};
+PreArgs plain_args(const GemmArgs& g) {
+  PreArgs a;
+  a.A = PlainMat{g.A.p, g.A.us};
+  a.B = PlainMat{g.B.p, g.B.us};
+  a.opA = g.opA;
+  a.opB = g.opB;
+  a.n = g.n;
+  a.active = g.active;
+  return a;
+}
+
+template <class ARGS>
+__device__ __forceinline__ void b_col_scales(const ARGS& g, int u, int* eb) {
   const int n = g.n;
   const zc* B = g.B.at(u);
   int* out = eb + (size_t)u * n;
@@ -1003,7 +1029,9 @@ __device__ __forceinline__ void b_col_scales(const GemmArgs& g, int u, int* eb) 
 // both pre-passes share one launch.
 constexpr int PRE_ROWS = 32;
 constexpr int PRE_OWN = 8;   // chunks owned per thread: n <= 2 * PRE_OWN * KC2 = 128
-__global__ void __launch_bounds__(256) oz_digitize_a2_kernel(GemmArgs g, OzImages im, int with_b) {
+// ARGS: PreArgs for operands in the plain layout, GemmArgs otherwise
+template <class ARGS>
+__global__ void __launch_bounds__(256) oz_digitize_a2_kernel(ARGS g, OzImages im, int with_b) {
   const int u = blockIdx.y;
   if (g.active && !g.active[u]) return;
   if (with_b && blockIdx.x == gridDim.x - 1) {
@@ -1615,7 +1643,10 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
   // A digit images and op(B)'s column scales in one launch (n <= 96 here)
-  oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
+  if (g.A.plain() && g.B.plain())
+    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(plain_args(g), im, 1);
+  else
+    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
@@ -1686,7 +1717,10 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
   // A digit images and op(B)'s column scales in one launch
-  oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
+  if (g.A.plain() && g.B.plain())
+    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(plain_args(g), im, 1);
+  else
+    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
@@ -1702,15 +1736,30 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
 // full-width tiles (one CTA per SM)
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 
-// blocks up to 96: half-width tiles (less padding, two CTAs per SM); 96 < n <= 128:
-// persistent full-width tiles with the epilogue overlapping the next tile's MMAs;
-// larger blocks: full-width tiles, one CTA per tile
-cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+bool oz_variant_supported(int n, int variant) {
+  if (!oz_supported(n)) return false;
+  switch (variant) {
+    case OZ_DEFAULT: return true;
+    case OZ_HALF: case OZ_PERSISTENT: return n <= 128;
+    case OZ_FULL: return true;
+    default: return false;
+  }
+}
+
+// the default rule: blocks up to 96: half-width tiles (less padding, two CTAs per SM);
+// 96 < n <= 128: persistent full-width tiles with the epilogue overlapping the next
+// tile's MMAs; larger blocks: full-width tiles, one CTA per tile
+cudaError_t zgemm_ozt_variant(const GemmArgs& g, void* scratch, int* err, cudaStream_t s, int variant) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
-  if (!scratch) return cudaErrorInvalidValue;
-  if (g.n <= 96) return zgemm_ozs(g, scratch, err, s);
-  if (g.n <= 128) return zgemm_ozp(g, scratch, err, s);
+  if (!scratch || !oz_variant_supported(g.n, variant)) return cudaErrorInvalidValue;
+  if (variant == OZ_DEFAULT) variant = g.n <= 96 ? OZ_HALF : g.n <= 128 ? OZ_PERSISTENT : OZ_FULL;
+  if (variant == OZ_HALF) return zgemm_ozs(g, scratch, err, s);
+  if (variant == OZ_PERSISTENT) return zgemm_ozp(g, scratch, err, s);
   return zgemm_ozt_full(g, scratch, err, s);
+}
+
+cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  return zgemm_ozt_variant(g, scratch, err, s, OZ_DEFAULT);
 }
 
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
@@ -1731,7 +1780,10 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
   im.eb = im.ea + (size_t)n * g.units;
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
-  oz_digitize_a_kernel<<<dim3(im.tiles_m * (TM / 32), g.units), 256, 0, s>>>(g, im);
+  if (g.A.plain() && g.B.plain())
+    oz_digitize_a_kernel<<<dim3(im.tiles_m * (TM / 32), g.units), 256, 0, s>>>(plain_args(g), im);
+  else
+    oz_digitize_a_kernel<<<dim3(im.tiles_m * (TM / 32), g.units), 256, 0, s>>>(g, im);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   oz_scale_kernel<<<dim3(1, g.units), 256, 0, s>>>(g, im.ea, im.eb, 1);   // column scales of op(B)

@@ -89,6 +89,32 @@ negf_status make_layout(Ctx* ctx, const negf_system* sys, Layout& L) {
   return NEGF_OK;
 }
 
+// the host-side work list of the devices `devs` (one block size) of an uneven batch:
+// unit u = (device, energy) in device-then-energy order; element offsets of each unit's
+// block 0 in the diagonal and off-diagonal outputs; its global energy index
+struct WorkList {
+  std::vector<int> unit_dev, unit_e, unit_nb, unit_glob;
+  std::vector<long long> off_d, off_o;
+};
+
+WorkList make_worklist(const negf_system* sys, const Layout& L, const std::vector<int>& devs, long long bb) {
+  WorkList w;
+  for (size_t k = 0; k < devs.size(); ++k) {
+    const int d = devs[k];
+    const long long* o = &L.off[8 * (size_t)d];
+    const long long nb = sys->nb[d];
+    for (int e = 0; e < sys->ne[d]; ++e) {
+      w.unit_dev.push_back((int)k);
+      w.unit_e.push_back(e);
+      w.unit_nb.push_back((int)nb);
+      w.unit_glob.push_back((int)(o[2] + e));
+      w.off_d.push_back(o[4] + (long long)e * nb * bb);
+      w.off_o.push_back(o[5] + (long long)e * (nb - 1) * bb);
+    }
+  }
+  return w;
+}
+
 negf_status check_system(Ctx* ctx, const negf_system* sys) {
   if (!sys->H_diag) return fail(ctx, NEGF_ERR_ARG, "H_diag is NULL");
   bool any_multi = false;
@@ -130,6 +156,14 @@ ScatView scat_view(const negf_scattering* sc, const Layout& L, int d, int nb, in
   return s;
 }
 
+// one device of an uneven batch as the batched sweeps over (device, energy) units see it
+struct UnitDev {
+  DevView dv;
+  ScatView sc;
+  const zc *sigma_L, *sigma_R;   // this device's lead blocks (energy 0)
+  const double *fL, *fR;         // this device's occupations (energy 0), nullable
+};
+
 // ---------------------------------------------------------------------------
 // assembly kernels (row a1 of the hot path): blocks of A = z S - H - Sigma and of
 // Sigma^< for the units of one step, written to workspace slots
@@ -141,6 +175,16 @@ struct AsmArgs {
   int units;
   int i_diag;        // diagonal block index (A_ii and Sigma^<_ii), -1 => none
   int i_off;         // upper block index j (A_{j,j+1} and A_{j+1,j}), -1 => none
+  // units are (energy, partition) pairs u = e P + p whose block indices are offset by
+  // p L (P = 1: one unit per energy); an off-diagonal index outside [0, nb-1) gives zero
+  // blocks
+  int P = 1, L = 0;
+  // units of an uneven batch: unit u is energy unit_e[u] of device udev[unit_dev[u]]
+  // (then dv, sc, e0, the lead pointers and occupations above are unused); a unit whose
+  // device has no block i_diag is skipped
+  const UnitDev* udev = nullptr;
+  const int* unit_dev = nullptr;
+  const int* unit_e = nullptr;
   zc *Adiag, *Aup, *Alow, *SigL;   // slot bases (unit stride b*b), each nullable
   zc* SigG;                        // Sigma^>_ii slot (nullable)
   const zc *sigma_L, *sigma_R;     // lead self-energies of this device, [ne] blocks
@@ -154,15 +198,30 @@ constexpr int ASM_T = 32;
 
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const int u = blockIdx.y;
+  int e;
+  if (a.udev) {   // the unit's own device
+    const UnitDev& D = a.udev[a.unit_dev[u]];
+    a.dv = D.dv;
+    a.sc = D.sc;
+    a.sigma_L = D.sigma_L;
+    a.sigma_R = D.sigma_R;
+    a.fL = D.fL;
+    a.fR = D.fR;
+    e = a.unit_e[u];
+    if (a.i_diag >= a.dv.nb || a.i_off >= a.dv.nb - 1) return;   // no such block in this device
+  } else {
+    e = a.e0 + u / a.P;
+  }
   const int b = a.dv.b, nb = a.dv.nb;
   const long long bb = (long long)b * b;
-  const int e = a.e0 + u;
+  const int poff = (u % a.P) * a.L;
   const zc z = zmake(a.dv.E[e], a.dv.eta);
   const int ntile = (b + ASM_T - 1) / ASM_T;
   const int r0 = (blockIdx.x / ntile) * ASM_T, c0 = (blockIdx.x % ntile) * ASM_T;
   const int tx = threadIdx.x, ty = threadIdx.y;
   __shared__ zc tS[ASM_T][ASM_T + 1], tH[ASM_T][ASM_T + 1];
-  const int i = a.i_diag, j = a.i_off;
+  const int i = a.i_diag + poff, j = a.i_off + poff;
+  const bool offv = j >= 0 && j < nb - 1;
   const bool lead_lesser = (a.SigL || a.SigG) && (i == 0 || i == nb - 1);
   const zc* sg = (i == 0) ? a.sigma_L + e * bb : a.sigma_R + e * bb;
   const double fo = (i == 0) ? (a.fL ? a.fL[e] : 0.0) : (a.fR ? a.fR[e] : 0.0);
@@ -173,7 +232,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
     for (int k = 0; k < ASM_T / 8; ++k) {
       const int rr = c0 + ty + 8 * k, cc = r0 + tx;
       zc sv = zmake(0.0, 0.0), hv = zmake(0.0, 0.0);
-      if (rr < b && cc < b) {
+      if (rr < b && cc < b && offv) {
         if (a.dv.Su) sv = a.dv.Su[j * bb + (long long)rr * b + cc];
         hv = a.dv.Hu[j * bb + (long long)rr * b + cc];
       }
@@ -196,12 +255,13 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
       a.Adiag[u * bb + rc] = v;
     }
     if (a.Aup) {   // A_{j,j+1} = z S_up - H_up
-      zc s = a.dv.Su ? a.dv.Su[j * bb + rc] : zmake(0.0, 0.0);
-      a.Aup[u * bb + rc] = zsub(zmul(z, s), a.dv.Hu[j * bb + rc]);
+      zc v = zmake(0.0, 0.0);
+      if (offv) v = zsub(zmul(z, a.dv.Su ? a.dv.Su[j * bb + rc] : zmake(0.0, 0.0)), a.dv.Hu[j * bb + rc]);
+      a.Aup[u * bb + rc] = v;
     }
     if (a.Alow) {  // A_{j+1,j} = z S_up^H - H_up^H: element (r, c) = conj of (c, r)
       const zc s = zconj(tS[ty + 8 * k][tx]);
-      a.Alow[u * bb + rc] = zsub(zmul(z, s), zconj(tH[ty + 8 * k][tx]));
+      a.Alow[u * bb + rc] = offv ? zsub(zmul(z, s), zconj(tH[ty + 8 * k][tx])) : zmake(0.0, 0.0);
     }
   }
   if (!a.SigL && !a.SigG) return;
@@ -259,8 +319,9 @@ cudaError_t assemble(const AsmArgs& a, cudaStream_t s) {
 }
 
 // D = D - W + W^H   (the anti-Hermitian completion of G^<_ii)
-__global__ void antiherm_update_kernel(BMat D, BMat W, int n) {
+__global__ void antiherm_update_kernel(BMat D, BMat W, int n, const int* act) {
   const int u = blockIdx.y;
+  if (act && !act[u]) return;
   const long long nn = (long long)n * n;
   zc* d = D.at(u);
   const zc* w = W.at(u);
@@ -271,11 +332,11 @@ __global__ void antiherm_update_kernel(BMat D, BMat W, int n) {
   }
 }
 
-cudaError_t antiherm_update(BMat D, BMat W, int n, int units, cudaStream_t s) {
+cudaError_t antiherm_update(BMat D, BMat W, int n, int units, cudaStream_t s, const int* act = nullptr) {
   if (units <= 0) return cudaSuccess;
   const long long nn = (long long)n * n;
   dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), units);
-  antiherm_update_kernel<<<grid, 256, 0, s>>>(D, W, n);
+  antiherm_update_kernel<<<grid, 256, 0, s>>>(D, W, n, act);
   return cudaGetLastError();
 }
 
@@ -289,8 +350,9 @@ __global__ void add_kernel(BMat D, BMat A, BMat B, int n, const int* act) {
 }
 
 // R = I - R  (R holds M X on entry)
-__global__ void one_minus_kernel(BMat R, int n) {
+__global__ void one_minus_kernel(BMat R, int n, const int* act) {
   const int u = blockIdx.y;
+  if (act && !act[u]) return;
   const long long nn = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / n), c = (int)(i - (long long)r * n);
@@ -313,7 +375,9 @@ struct Engine {
     return ozt_scratch ? oz_supported(n) : (oz_scratch != nullptr && oz_inkernel_supported(n));
   }
   cudaError_t sliced(const GemmArgs& g) {
-    return ozt_scratch ? zgemm_ozt(g, ozt_scratch, ctx->d_err, s) : zgemm_oz(g, oz_scratch, ctx->d_err, s);
+    if (!ozt_scratch) return zgemm_oz(g, oz_scratch, ctx->d_err, s);
+    const int v = (g.n >= 0 && g.n <= 512) ? ctx->oz_variant[g.n] : OZ_DEFAULT;
+    return zgemm_ozt_variant(g, ozt_scratch, ctx->d_err, s, v);
   }
   // timing facility: events around one launch of class `cls`
   int open_cls = -1;
@@ -332,6 +396,9 @@ struct Engine {
     ctx->recs.push_back(ProfRec{open_cls, open_ev, e1, flops, bytes});
     open_cls = -1;
   }
+  // share of the units a masked launch works on, when the caller knows it (the batched
+  // sweeps of an uneven batch); < 0: unknown (such launches are counted as "other")
+  double active_frac = -1.0;
   cudaError_t gemm(BMat D, BMat A, int opA, BMat B, int opB, zc alpha, BMat C, zc beta, int n, int units,
                    const int* active = nullptr) {
     GemmArgs g;
@@ -339,10 +406,11 @@ struct Engine {
     g.opA = opA; g.opB = opB; g.alpha = alpha; g.beta = beta;
     g.n = n; g.units = units; g.active = active;
     const double nn = (double)n * n;
-    const double flops = 8.0 * nn * n * units;                        // useful complex flops
-    const double bytes = 16.0 * nn * units * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
+    const double frac = (active && active_frac >= 0.0) ? active_frac : 1.0;
+    const double flops = 8.0 * nn * n * units * frac;                        // useful complex flops
+    const double bytes = 16.0 * nn * units * frac * (3.0 + (C.p ? 1.0 : 0.0));   // A, B, D (+C) once each
     cudaError_t e;
-    const bool masked = active != nullptr;   // masked launches do an unknown share of the work
+    const bool masked = active != nullptr && active_frac < 0.0;   // an unknown share of the work
     if (mixed == 1 && can_slice(n)) {
       begin(masked ? K_OTHER : K_GEMM_OZ);
       e = sliced(g);
@@ -357,10 +425,11 @@ struct Engine {
     return e;
   }
   cudaError_t inv(BMat X, BMat M, int n, int units, const int* active, int single, int32_t* status) {
-    const bool masked = active != nullptr;   // masked launches do an unknown share of the work
+    const bool masked = active != nullptr && active_frac < 0.0;   // an unknown share of the work
+    const double frac = (active && active_frac >= 0.0) ? active_frac : 1.0;
     begin(masked ? K_OTHER : (single ? K_INV_F32 : K_INV_F64));
     cudaError_t e = zinv(X, M, n, units, active, single, inv_scratch, status, s);
-    end(masked ? 0.0 : 8.0 * (double)n * n * n * units, masked ? 0.0 : 32.0 * (double)n * n * units);
+    end(masked ? 0.0 : 8.0 * (double)n * n * n * units * frac, masked ? 0.0 : 32.0 * (double)n * n * units * frac);
     return e;
   }
   // X = M^{-1}.  Mixed precision: FP32 Gauss-Jordan, then `refine` steps of
@@ -368,9 +437,10 @@ struct Engine {
   // correction product on the engine's GEMM.  T1, T2: scratch slots.
   // Refinement steps: two with the sliced product (each step squares the relative
   // error of the FP32 inverse, so kappa ~ 1e6 blocks need two), one with the TF32 mode.
-  cudaError_t inverse(BMat X, BMat M, int n, int units, int32_t* status, BMat T1, BMat T2, int refine = -1) {
+  cudaError_t inverse(BMat X, BMat M, int n, int units, int32_t* status, BMat T1, BMat T2, int refine = -1,
+                      const int* active = nullptr) {
     if (refine < 0) refine = (mixed == 1) ? 2 : 1;
-    cudaError_t e = inv(X, M, n, units, nullptr, mixed ? 1 : 0, status);
+    cudaError_t e = inv(X, M, n, units, active, mixed ? 1 : 0, status);
     if (e != cudaSuccess || !mixed) return e;
     const long long nn = (long long)n * n;
     dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), units);
@@ -378,7 +448,8 @@ struct Engine {
       GemmArgs r;
       r.D = T1; r.A = M; r.B = X; r.C = BMat{nullptr, 0};
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
-      r.n = n; r.units = units; r.active = nullptr;
+      r.n = n; r.units = units; r.active = active;
+      const double frac = (active && active_frac >= 0.0) ? active_frac : 1.0;
       // M X with FP64-class accuracy: the sliced tensor-core product, else FP64 FMA
       if (mixed == 1 && can_slice(n)) {
         begin(K_GEMM_OZ);
@@ -387,24 +458,24 @@ struct Engine {
         begin(K_GEMM_F64);
         e = zgemm_f64(r, s);
       }
-      end(8.0 * (double)n * n * n * units, 48.0 * (double)n * n * units);
+      end(8.0 * (double)n * n * n * units * frac, 48.0 * (double)n * n * units * frac);
       if (e != cudaSuccess) return e;
       ++ctx->launches;
-      one_minus_kernel<<<grid, 256, 0, s>>>(T1, n);                        // I - M X
+      one_minus_kernel<<<grid, 256, 0, s>>>(T1, n, active);               // I - M X
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if (mixed == 1 && ozt_scratch && oz_supported(n)) {
         // X <- X + X (I - M X) in one product: these kernels read op(A) only through the
         // digit images made before they start, and C and D element by element in one
         // thread, so D, A and C may all be X
-        if ((e = gemm(X, X, OP_N, T1, OP_N, zmake(1.0, 0.0), X, zmake(1.0, 0.0), n, units)) != cudaSuccess)
+        if ((e = gemm(X, X, OP_N, T1, OP_N, zmake(1.0, 0.0), X, zmake(1.0, 0.0), n, units, active)) != cudaSuccess)
           return e;
         continue;
       }
-      if ((e = gemm(T2, X, OP_N, T1, OP_N, zmake(1.0, 0.0), BMat{nullptr, 0}, zmake(0.0, 0.0), n, units)) !=
+      if ((e = gemm(T2, X, OP_N, T1, OP_N, zmake(1.0, 0.0), BMat{nullptr, 0}, zmake(0.0, 0.0), n, units, active)) !=
           cudaSuccess)
         return e;                                                          // X (I - M X)
       ++ctx->launches;
-      add_kernel<<<grid, 256, 0, s>>>(X, X, T2, n, nullptr);
+      add_kernel<<<grid, 256, 0, s>>>(X, X, T2, n, active);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -429,9 +500,30 @@ struct RgfIO {
   bool greater = false;          // also G^> (with `lesser`)
 };
 
+// The (device, energy) units of the devices of an uneven batch that share one block size,
+// for batched sweeps over all of them (Sec. II: every energy of every device is
+// independent): device-side tables in the workspace.  Step i of the forward sweep runs
+// on the units whose device has block i, step i of the backward sweep on those with
+// block i+1; each launch covers every unit of the group, the others masked out.
+struct BatchPlan {
+  int nb;                      // the largest block count of the group: the sweeps' length
+  const UnitDev* udev;         // [devices of the group]
+  const int* unit_dev;         // [U] index into udev
+  const int* unit_e;           // [U] device-local energy
+  const long long* off_d;      // [U] element offset of the unit's block 0 in GR_diag / GL_diag / GG_diag
+  const long long* off_o;      // [U] element offset of the unit's block 0 in the off-diagonal outputs
+  const int* act_f;            // [nb][U]: forward step i active (i < nb of the unit's device)
+  const int* act_b;            // [nb][U]: backward step i active (i <= nb - 2)
+  const double* frac_f;        // host [nb]: share of the units active at forward step i
+  const double* frac_b;        // host [nb]: ... at backward step i
+  int32_t* st_units;           // [U] per-unit status
+};
+
 negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& sc, const RgfIO& io, int e0,
-                      int U, char* ws) {
-  const int nb = dv.nb, b = dv.b;
+                      int U, char* ws, const BatchPlan* bp = nullptr, int out_e0 = -1) {
+  // the output buffers' first block is energy eo's (e0: the caller's full arrays)
+  const int eo = out_e0 < 0 ? e0 : out_e0;
+  const int nb = bp ? bp->nb : dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
   const size_t blk = sizeof(zc) * bb;
   cudaStream_t s = eng.s;
@@ -459,19 +551,15 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   eng.ozt_scratch = (void*)p;
 
   auto S1 = [&](zc* base) { return BMat{base, bb}; };
-  // per-energy output blocks: [e][i] with unit stride nb*b*b (diag) or (nb-1)*b*b (off-diagonal)
-  auto gD = [&](int i) {
-    return io.GRd ? BMat{io.GRd + ((long long)e0 * nb + i) * bb, (long long)nb * bb}
-                  : BMat{gbase + (long long)i * U * bb, bb};
+  // per-energy output blocks: [e][i] with unit stride nb*b*b (diag) or (nb-1)*b*b (off-diagonal);
+  // for an uneven batch, block i of unit u at base + off[u] + i b*b
+  auto outD = [&](zc* base, int i) {
+    if (bp) return BMat{base + (long long)i * bb, 0, 0, 0, bp->off_d};
+    return BMat{base + ((long long)(e0 - eo) * nb + i) * bb, (long long)nb * bb};
   };
-  auto glD = [&](int i) {
-    return io.GLd ? BMat{io.GLd + ((long long)e0 * nb + i) * bb, (long long)nb * bb}
-                  : BMat{glbase + (long long)i * U * bb, bb};
-  };
-  auto ggD = [&](int i) {
-    return io.GGd ? BMat{io.GGd + ((long long)e0 * nb + i) * bb, (long long)nb * bb}
-                  : BMat{ggbase + (long long)i * U * bb, bb};
-  };
+  auto gD = [&](int i) { return io.GRd ? outD(io.GRd, i) : BMat{gbase + (long long)i * U * bb, bb}; };
+  auto glD = [&](int i) { return io.GLd ? outD(io.GLd, i) : BMat{glbase + (long long)i * U * bb, bb}; };
+  auto ggD = [&](int i) { return io.GGd ? outD(io.GGd, i) : BMat{ggbase + (long long)i * U * bb, bb}; };
   auto Yb = [&](int i) { return BMat{Ybase + (long long)i * U * bb, bb}; };
   // the Keldysh kinds of this call: G^< and, with `greater`, G^> (the same recursion on
   // Sigma^> in place of Sigma^<)
@@ -479,15 +567,21 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   std::vector<Kind> kinds;
   if (io.lesser) kinds.push_back(Kind{SigL, glD, io.GLl});
   if (greater) kinds.push_back(Kind{SigG, ggD, io.GGl});
-  auto offB = [&](zc* base, int i) { return BMat{base + ((long long)e0 * (nb - 1) + i) * bb, (long long)(nb - 1) * bb}; };
+  auto offB = [&](zc* base, int i) {
+    if (bp) return BMat{base + (long long)i * bb, 0, 0, 0, bp->off_o};
+    return BMat{base + ((long long)(e0 - eo) * (nb - 1) + i) * bb, (long long)(nb - 1) * bb};
+  };
 
   AsmArgs a;
   a.dv = dv; a.sc = sc; a.e0 = e0; a.units = U;
   a.sigma_L = io.sigma_L; a.sigma_R = io.sigma_R; a.fL = io.fL; a.fR = io.fR;
-  int32_t* st = io.status ? io.status + e0 : nullptr;
+  if (bp) { a.udev = bp->udev; a.unit_dev = bp->unit_dev; a.unit_e = bp->unit_e; }
+  int32_t* st = bp ? bp->st_units : (io.status ? io.status + e0 : nullptr);
+  const int* act = nullptr;   // this step's mask (uneven batch), else every unit
 
   // ---------------- forward sweep
   for (int i = 0; i < nb; ++i) {
+    if (bp) { act = bp->act_f + (size_t)i * U; eng.active_frac = bp->frac_f[i]; }
     a.i_diag = i;
     a.i_off = i - 1;
     a.Adiag = Adiag; a.SigL = SigL; a.SigG = SigG;
@@ -496,28 +590,29 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     ++ctx->launches;
     CU(assemble(a, s));
     if (i == 0) {
-      CU(eng.inverse(gD(0), S1(Adiag), b, U, st, S1(T[1]), S1(T[2])));
+      CU(eng.inverse(gD(0), S1(Adiag), b, U, st, S1(T[1]), S1(T[2]), -1, act));
       for (const Kind& k : kinds) {
-        CU(eng.gemm(S1(T[2]), gD(0), OP_N, S1(k.sig), OP_N, ONE, NOMAT, ZERO, b, U));
-        CU(eng.gemm(k.D(0), S1(T[2]), OP_N, gD(0), OP_H, ONE, NOMAT, ZERO, b, U));
+        CU(eng.gemm(S1(T[2]), gD(0), OP_N, S1(k.sig), OP_N, ONE, NOMAT, ZERO, b, U, act));
+        CU(eng.gemm(k.D(0), S1(T[2]), OP_N, gD(0), OP_H, ONE, NOMAT, ZERO, b, U, act));
       }
       continue;
     }
     // Y_{i-1} = A_{i,i-1} g_{i-1};  M = A_ii - Y_{i-1} A_{i-1,i};  g_i = M^{-1}
-    CU(eng.gemm(Yb(i - 1), S1(Alow), OP_N, gD(i - 1), OP_N, ONE, NOMAT, ZERO, b, U));
-    CU(eng.gemm(S1(T[0]), Yb(i - 1), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, U));
-    CU(eng.inverse(gD(i), S1(T[0]), b, U, st, S1(T[1]), S1(T[2])));
+    CU(eng.gemm(Yb(i - 1), S1(Alow), OP_N, gD(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act));
+    CU(eng.gemm(S1(T[0]), Yb(i - 1), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, U, act));
+    CU(eng.inverse(gD(i), S1(T[0]), b, U, st, S1(T[1]), S1(T[2]), -1, act));
     for (const Kind& k : kinds) {
       // g^x_i = g_i (Sigma^x_ii + A_{i,i-1} g^x_{i-1} A_{i,i-1}^H) g_i^H   (x = <, >)
-      CU(eng.gemm(S1(T[1]), S1(Alow), OP_N, k.D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(S1(T[2]), S1(T[1]), OP_N, S1(Alow), OP_H, ONE, S1(k.sig), ONE, b, U));
-      CU(eng.gemm(S1(T[3]), gD(i), OP_N, S1(T[2]), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(k.D(i), S1(T[3]), OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(S1(T[1]), S1(Alow), OP_N, k.D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(S1(T[2]), S1(T[1]), OP_N, S1(Alow), OP_H, ONE, S1(k.sig), ONE, b, U, act));
+      CU(eng.gemm(S1(T[3]), gD(i), OP_N, S1(T[2]), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(k.D(i), S1(T[3]), OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U, act));
     }
   }
   // ---------------- backward sweep
   a.Adiag = nullptr; a.SigL = nullptr; a.SigG = nullptr;
   for (int i = nb - 2; i >= 0; --i) {
+    if (bp) { act = bp->act_b + (size_t)i * U; eng.active_frac = bp->frac_b[i]; }
     a.i_diag = -1;
     a.i_off = i;
     a.Aup = Aup; a.Alow = Alow;
@@ -526,22 +621,367 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     const BMat X = S1(T[0]);
     const BMat Gup = io.GRu ? offB(io.GRu, i) : S1(gup_tmp);
     // X = g_i A_{i,i+1};  G_{i,i+1} = -X G_{i+1,i+1};  G_ii = g_i - G_{i,i+1} Y_i;  G_{i+1,i} = -G_{i+1,i+1} Y_i
-    CU(eng.gemm(X, gD(i), OP_N, S1(Aup), OP_N, ONE, NOMAT, ZERO, b, U));
-    CU(eng.gemm(Gup, X, OP_N, gD(i + 1), OP_N, MONE, NOMAT, ZERO, b, U));
-    CU(eng.gemm(gD(i), Gup, OP_N, Yb(i), OP_N, MONE, gD(i), ONE, b, U));
-    if (io.GRl) CU(eng.gemm(offB(io.GRl, i), gD(i + 1), OP_N, Yb(i), OP_N, MONE, NOMAT, ZERO, b, U));
+    CU(eng.gemm(X, gD(i), OP_N, S1(Aup), OP_N, ONE, NOMAT, ZERO, b, U, act));
+    CU(eng.gemm(Gup, X, OP_N, gD(i + 1), OP_N, MONE, NOMAT, ZERO, b, U, act));
+    CU(eng.gemm(gD(i), Gup, OP_N, Yb(i), OP_N, MONE, gD(i), ONE, b, U, act));
+    if (io.GRl) CU(eng.gemm(offB(io.GRl, i), gD(i + 1), OP_N, Yb(i), OP_N, MONE, NOMAT, ZERO, b, U, act));
     for (const Kind& k : kinds) {
       const BMat Z = S1(T[1]), P = S1(T[2]), Wm = S1(T[3]);
       // Z = A_{i+1,i} g^x_i;  P = G^x_{i+1,i+1} X^H;  W = G_{i,i+1} Z   (x = <, >)
-      CU(eng.gemm(Z, S1(Alow), OP_N, k.D(i), OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(P, k.D(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(Z, S1(Alow), OP_N, k.D(i), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(P, k.D(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U, act));
       // G^x_ii = g^x_i + X P - W + W^H
-      CU(eng.gemm(k.D(i), X, OP_N, P, OP_N, ONE, k.D(i), ONE, b, U));
+      CU(eng.gemm(k.D(i), X, OP_N, P, OP_N, ONE, k.D(i), ONE, b, U, act));
       ++ctx->launches;
-      CU(antiherm_update(k.D(i), Wm, b, U, s));
+      CU(antiherm_update(k.D(i), Wm, b, U, s, act));
       // G^x_{i+1,i} = -G_{i+1,i+1} Z - P
-      if (k.low) CU(eng.gemm(offB(k.low, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U));
+      if (k.low) CU(eng.gemm(offB(k.low, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U, act));
+    }
+  }
+  eng.active_frac = -1.0;
+  return NEGF_OK;
+}
+
+// dst[u] = src[u] (units of any BMat layout)
+__global__ void bcopy_kernel(BMat dst, BMat src, int n) {
+  const int u = blockIdx.y;
+  const long long nn = (long long)n * n;
+  zc* d = dst.at(u);
+  const zc* q = src.at(u);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+    d[i] = q[i];
+}
+
+cudaError_t bcopy(BMat dst, BMat src, int n, int units, cudaStream_t s) {
+  if (units <= 0) return cudaSuccess;
+  const long long nn = (long long)n * n;
+  bcopy_kernel<<<dim3((unsigned)std::min<long long>((nn + 255) / 256, 1024), units), 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+// status[e] = the worst (most negative) code of the units e*P .. e*P+P-1
+__global__ void status_merge_kernel(int32_t* status, const int32_t* st_units, int U, int P) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= U) return;
+  int32_t w = status[e];
+  for (int p = 0; p < P; ++p) w = min(w, st_units[(long long)e * P + p]);
+  status[e] = w;
+}
+
+// ---------------------------------------------------------------------------
+// partitioned selected inversion of G^R (Sec. II, Fig. 3): P partitions of L = nb/P
+// blocks, one unit per (energy, partition) u = e P + p, so that every step is one
+// batched launch over U P units.  Partition p eliminates its interior blocks
+// pL .. pL+L-2 downward with the previous partition's last block e_(p-1) = pL-1 as the
+// top boundary a and its own last block e_p = pL+L-1 as the bottom boundary b:
+//   g_k = D_k^{-1};  Y_k = A_ji g_k, X_k = g_k A_ij, Xa_k = F_ak g_k, Wa_k = g_k F_ka;
+//   D_j = A_jj - Y_k A_ij, F_aj = -Xa_k A_ij, F_ja = -Y_k F_ka, dD_a -= Xa_k F_ka
+// (F = 0 for p = 0).  The boundaries e_0 .. e_(P-1) form a BT system with diagonal
+// D_(e_r) + dD_a of partition r+1 and couplings F_ab, F_ba of partition r+1, inverted
+// by the block recursion (one unit per energy).  Each partition then rebuilds its
+// interior from the boundary blocks of G, k = L-2 .. 0, j = k+1:
+//   G_jk = -(G_ja Xa_k + G_jj Y_k), G_ak = -(G_aa Xa_k + G_aj Y_k),
+//   G_kj = -(Wa_k G_aj + X_k G_jj), G_ka = -(Wa_k G_aa + X_k G_ja),
+//   G_kk = g_k - (Wa_k G_ak + X_k G_jk),
+// and G_(a,pL), G_(pL,a) are the off-diagonal blocks between partitions.
+// ---------------------------------------------------------------------------
+size_t partitioned_bytes_per_energy(int nb, int b, int P, int mixed) {
+  const int L = nb / P;
+  const size_t blk = sizeof(zc) * (size_t)b * b;
+  // per (energy, partition): 17 working slots + 4 (L - 1) stored factors; per energy:
+  // 2 (P - 1) reduced-recursion slots + 1; per unit status word
+  size_t bytes = blk * ((size_t)P * (17 + 4 * (size_t)(L - 1)) + 2 * (size_t)std::max(P - 1, 1) + 1);
+  bytes += sizeof(int32_t) * (size_t)P + 256;
+  bytes += zinv_scratch_bytes(b, P, mixed ? 1 : 0);
+  if (mixed == 1) bytes += ozt_scratch_bytes(b, P) + 1024;
+  return bytes;
+}
+
+negf_status rgf_partitioned_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& sc, const RgfIO& io,
+                                  int P, int e0, int U, char* ws) {
+  const int nb = dv.nb, b = dv.b, L = nb / P, UP = U * P;
+  const long long bb = (long long)b * b;
+  const size_t blk = sizeof(zc) * bb;
+  cudaStream_t s = eng.s;
+  char* p = ws;
+  auto slots = [&](long long count) { zc* q = (zc*)p; p += blk * (size_t)count; return q; };
+  auto S1 = [&](zc* base) { return BMat{base, bb}; };
+  zc *Adiag = slots(UP), *Aup = slots(UP), *Alow = slots(UP), *D = slots(UP), *dDa = slots(UP);
+  zc *Fak = slots(UP), *Fka = slots(UP), *Fak2 = slots(UP), *Fka2 = slots(UP);
+  zc *T0 = slots(UP), *T1 = slots(UP), *T2 = slots(UP);
+  zc *Gaa = slots(UP), *Gaj = slots(UP), *Gja = slots(UP), *Gak = slots(UP), *Gka = slots(UP);
+  zc* Yf = slots((long long)UP * (L - 1));
+  zc* Xf = slots((long long)UP * (L - 1));
+  zc* Xaf = slots((long long)UP * (L - 1));
+  zc* Waf = slots((long long)UP * (L - 1));
+  zc* RY = slots((long long)U * std::max(P - 1, 1));   // reduced recursion: A_(r+1,r) g_r per energy
+  zc* RX = slots(U);
+  int32_t* st_units = (int32_t*)p;
+  p += ((sizeof(int32_t) * (size_t)UP + 255) / 256) * 256;
+  if (zinv_scratch_bytes(b, UP, eng.mixed ? 1 : 0) > 0) {
+    eng.inv_scratch = (void*)p;
+    p += zinv_scratch_bytes(b, UP, eng.mixed ? 1 : 0);
+  }
+  p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+  eng.ozt_scratch = (void*)p;
+
+  // outputs seen per (energy, partition) unit: block pL + k of energy e0 + e
+  auto outD = [&](int k) { return BMat{io.GRd + ((long long)e0 * nb + k) * bb, (long long)nb * bb, P, L * bb}; };
+  auto outU = [&](zc* base, int k) {
+    return BMat{base + ((long long)e0 * (nb - 1) + k) * bb, (long long)(nb - 1) * bb, P, L * bb};
+  };
+  auto fac = [&](zc* base, int k) { return BMat{base + (long long)k * UP * bb, bb}; };
+  // per energy, the entry of partition r of a [U P] slot
+  auto ofP = [&](zc* base, int r) { return BMat{base + (long long)r * bb, (long long)P * bb}; };
+  // per energy, the output block e_r = rL + L - 1
+  auto redD = [&](int r) { return BMat{io.GRd + ((long long)e0 * nb + (long long)r * L + L - 1) * bb, (long long)nb * bb}; };
+  auto RYb = [&](int r) { return BMat{RY + (long long)r * U * bb, bb}; };
+
+  CU(cudaMemsetAsync(st_units, 0, sizeof(int32_t) * (size_t)UP, s));
+  AsmArgs a;
+  a.dv = dv; a.sc = sc; a.e0 = e0; a.units = UP; a.P = P; a.L = L;
+  a.sigma_L = io.sigma_L; a.sigma_R = io.sigma_R; a.fL = nullptr; a.fR = nullptr;
+  a.SigL = nullptr; a.SigG = nullptr;
+  // ---------------- elimination of the interiors, all partitions at once
+  a.i_diag = 0; a.i_off = -1;                    // D_0 = A_(pL,pL); F_a0, F_0a = A_(pL-1,pL), A_(pL,pL-1)
+  a.Adiag = D; a.Aup = Fak; a.Alow = Fka;
+  ++ctx->launches;
+  CU(assemble(a, s));
+  CU(cudaMemsetAsync(dDa, 0, blk * (size_t)UP, s));
+  for (int k = 0; k + 1 < L; ++k) {
+    CU(eng.inverse(outD(k), S1(D), b, UP, st_units, S1(T1), S1(T2)));      // g_k (in the G_kk output)
+    a.i_diag = k + 1; a.i_off = k;
+    a.Adiag = Adiag; a.Aup = Aup; a.Alow = Alow;
+    ++ctx->launches;
+    CU(assemble(a, s));                                                     // A_jj, A_ij, A_ji
+    CU(eng.gemm(fac(Yf, k), S1(Alow), OP_N, outD(k), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(fac(Xf, k), outD(k), OP_N, S1(Aup), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(fac(Xaf, k), S1(Fak), OP_N, outD(k), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(fac(Waf, k), outD(k), OP_N, S1(Fka), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(S1(D), fac(Yf, k), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, UP));      // D_j
+    CU(eng.gemm(S1(dDa), fac(Xaf, k), OP_N, S1(Fka), OP_N, MONE, S1(dDa), ONE, b, UP));     // dD_a
+    CU(eng.gemm(S1(Fak2), fac(Xaf, k), OP_N, S1(Aup), OP_N, MONE, NOMAT, ZERO, b, UP));     // F_aj
+    CU(eng.gemm(S1(Fka2), fac(Yf, k), OP_N, S1(Fka), OP_N, MONE, NOMAT, ZERO, b, UP));      // F_ja
+    std::swap(Fak, Fak2);
+    std::swap(Fka, Fka2);
+  }
+  // ---------------- the reduced BT system over the boundaries, one unit per energy
+  int32_t* st = io.status ? io.status + e0 : nullptr;
+  for (int r = 0; r < P; ++r) {
+    BMat M = ofP(D, r);
+    if (r + 1 < P) {                                                        // + dD_a of partition r+1
+      ++ctx->launches;
+      const long long nn = bb;
+      add_kernel<<<dim3((unsigned)std::min<long long>((nn + 255) / 256, 1024), U), 256, 0, s>>>(
+          S1(T0), ofP(D, r), ofP(dDa, r + 1), b, nullptr);
+      CU(cudaGetLastError());
+      M = S1(T0);
+    }
+    if (r > 0)                                                              // - A_(r,r-1) g_(r-1) A_(r-1,r)
+      CU(eng.gemm(S1(T0), RYb(r - 1), OP_N, ofP(Fak, r), OP_N, MONE, M, ONE, b, U));
+    CU(eng.inverse(redD(r), (r > 0 || r + 1 < P) ? S1(T0) : M, b, U, st, S1(T1), S1(T2)));
+    if (r + 1 < P) CU(eng.gemm(RYb(r), ofP(Fka, r + 1), OP_N, redD(r), OP_N, ONE, NOMAT, ZERO, b, U));
+  }
+  // G_aa, G_ab, G_ba of partition p (= G at e_(p-1), G_(e_(p-1), e_p), G_(e_p, e_(p-1))); zero for p = 0
+  CU(cudaMemsetAsync(Gaa, 0, blk * (size_t)UP, s));
+  CU(cudaMemsetAsync(Gaj, 0, blk * (size_t)UP, s));
+  CU(cudaMemsetAsync(Gja, 0, blk * (size_t)UP, s));
+  for (int r = P - 2; r >= 0; --r) {
+    // X = g_r A_(r,r+1); G_(r,r+1) = -X G_(r+1,r+1); G_(r+1,r) = -G_(r+1,r+1) Y_r; G_rr = g_r - G_(r,r+1) Y_r
+    CU(eng.gemm(S1(RX), redD(r), OP_N, ofP(Fak, r + 1), OP_N, ONE, NOMAT, ZERO, b, U));
+    CU(eng.gemm(ofP(Gaj, r + 1), S1(RX), OP_N, redD(r + 1), OP_N, MONE, NOMAT, ZERO, b, U));
+    CU(eng.gemm(ofP(Gja, r + 1), redD(r + 1), OP_N, RYb(r), OP_N, MONE, NOMAT, ZERO, b, U));
+    CU(eng.gemm(redD(r), ofP(Gaj, r + 1), OP_N, RYb(r), OP_N, MONE, redD(r), ONE, b, U));
+    ++ctx->launches;
+    CU(bcopy(ofP(Gaa, r + 1), redD(r), b, U, s));
+  }
+  // ---------------- reconstruction of the interiors, all partitions at once
+  zc* GRu = io.GRu;
+  zc* GRl = io.GRl;
+  for (int k = L - 2; k >= 0; --k) {
+    const BMat Gjj = outD(k + 1);
+    // G_jk = -(G_ja Xa_k) - G_jj Y_k
+    CU(eng.gemm(S1(T0), S1(Gja), OP_N, fac(Xaf, k), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(outU(GRl, k), Gjj, OP_N, fac(Yf, k), OP_N, MONE, S1(T0), MONE, b, UP));
+    // G_ak = -(G_aa Xa_k) - G_aj Y_k
+    CU(eng.gemm(S1(T0), S1(Gaa), OP_N, fac(Xaf, k), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(S1(Gak), S1(Gaj), OP_N, fac(Yf, k), OP_N, MONE, S1(T0), MONE, b, UP));
+    // G_kj = -(Wa_k G_aj) - X_k G_jj
+    CU(eng.gemm(S1(T0), fac(Waf, k), OP_N, S1(Gaj), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(outU(GRu, k), fac(Xf, k), OP_N, Gjj, OP_N, MONE, S1(T0), MONE, b, UP));
+    // G_ka = -(Wa_k G_aa) - X_k G_ja
+    CU(eng.gemm(S1(T0), fac(Waf, k), OP_N, S1(Gaa), OP_N, ONE, NOMAT, ZERO, b, UP));
+    CU(eng.gemm(S1(Gka), fac(Xf, k), OP_N, S1(Gja), OP_N, MONE, S1(T0), MONE, b, UP));
+    // G_kk = g_k - Wa_k G_ak - X_k G_jk   (in place over g_k)
+    CU(eng.gemm(outD(k), fac(Waf, k), OP_N, S1(Gak), OP_N, MONE, outD(k), ONE, b, UP));
+    CU(eng.gemm(outD(k), fac(Xf, k), OP_N, outU(GRl, k), OP_N, MONE, outD(k), ONE, b, UP));
+    std::swap(Gaj, Gak);
+    std::swap(Gja, Gka);
+  }
+  // the blocks between partitions: (pL-1, pL) = G_(a,pL), (pL, pL-1) = G_(pL,a), p >= 1
+  if (P > 1) {
+    const BMat dstU{GRu + ((long long)e0 * (nb - 1) + L - 1) * bb, (long long)(nb - 1) * bb, P - 1, L * bb};
+    const BMat dstL{GRl + ((long long)e0 * (nb - 1) + L - 1) * bb, (long long)(nb - 1) * bb, P - 1, L * bb};
+    const BMat srcU{Gaj + bb, (long long)P * bb, P - 1, bb};
+    const BMat srcL{Gja + bb, (long long)P * bb, P - 1, bb};
+    ctx->launches += 2;
+    CU(bcopy(dstU, srcU, b, U * (P - 1), s));
+    CU(bcopy(dstL, srcL, b, U * (P - 1), s));
+  }
+  if (st) {
+    ++ctx->launches;
+    status_merge_kernel<<<(U + 127) / 128, 128, 0, s>>>(st, st_units, U, P);
+    CU(cudaGetLastError());
+  }
+  return NEGF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// arrowhead BT (BTA): the device's BT matrix bordered by a tip block t (a gate, size b,
+// overlap I) coupled to every block: A_tt = z I - H_tip, A_(t,i) = -H_(t,i),
+// A_(i,t) = -H_(t,i)^H.  All device blocks are eliminated downward with the tip as the
+// boundary every block couples to (the partitioned recursions with a = t, plus the
+// arrow's own coupling at every block):
+//   D_0 = A_00, F_t0 = A_t0, F_0t = A_0t;  g_k = D_k^{-1}, Xt_k = F_tk g_k, Wt_k = g_k F_kt,
+//   dD_t -= Xt_k F_kt;  for j = k+1: Y_k = A_jk g_k, X_k = g_k A_kj, D_j = A_jj - Y_k A_kj,
+//   F_tj = A_tj - Xt_k A_kj, F_jt = A_jt - Y_k F_kt;
+// then G_tt = (A_tt + dD_t)^{-1}, and from the last block up:
+//   G_tk = -(G_tt Xt_k + G_tj Y_k),  G_kt = -(Wt_k G_tt + X_k G_jt),
+//   G_jk = -(G_jt Xt_k + G_jj Y_k),  G_kj = -(Wt_k G_tj + X_k G_jj),
+//   G_kk = g_k - (Wt_k G_tk + X_k G_jk)      (the j terms absent for the last block).
+// ---------------------------------------------------------------------------
+__global__ void tip_assemble_kernel(BMat Att, const zc* H_tip, const double* E, double eta, int e0, int n) {
+  const int u = blockIdx.y;
+  const zc z = zmake(E[e0 + u], eta);
+  const long long nn = (long long)n * n;
+  zc* d = Att.at(u);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn; k += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(k / n), c = (int)(k - (long long)r * n);
+    zc v = zmake(-H_tip[k].x, -H_tip[k].y);
+    if (r == c) v = zadd(v, z);
+    d[k] = v;
+  }
+}
+
+// the arrow's blocks of A, shared by all energies: row[i] = -H_(t,i), col[i] = -H_(t,i)^H
+__global__ void arrow_blocks_kernel(zc* row, zc* col, const zc* H, int n) {
+  const int i = blockIdx.y;
+  const long long nn = (long long)n * n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn; k += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(k / n), c = (int)(k - (long long)r * n);
+    const zc h = H[(long long)i * nn + k];
+    const zc ht = H[(long long)i * nn + (long long)c * n + r];
+    row[(long long)i * nn + k] = zmake(-h.x, -h.y);
+    col[(long long)i * nn + k] = zmake(-ht.x, ht.y);
+  }
+}
+
+struct ArrowIO {
+  const zc* H_tip;     // this device's tip Hamiltonian
+  const zc* H_arrow;   // this device's [nb] blocks H_(t,i)
+  zc *Gt, *Grow, *Gcol;   // device-offset outputs: [ne] tip blocks, [ne][nb] G_(t,i), G_(i,t)
+};
+
+size_t arrowhead_bytes_per_energy(int nb, int b, int mixed) {
+  const size_t blk = sizeof(zc) * (size_t)b * b;
+  size_t bytes = blk * (13 + 4 * (size_t)nb);
+  bytes += zinv_scratch_bytes(b, 1, mixed ? 1 : 0);
+  if (mixed == 1) bytes += ozt_scratch_bytes(b, 1) + 1024;
+  return bytes;
+}
+
+// Arow, Acol: the device's shared arrow blocks of A (arrow_blocks_kernel)
+negf_status rgf_arrowhead_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& sc, const RgfIO& io,
+                                const ArrowIO& ar, const zc* Arow, const zc* Acol, int e0, int U, char* ws) {
+  const int nb = dv.nb, b = dv.b;
+  const long long bb = (long long)b * b;
+  const size_t blk = sizeof(zc) * bb;
+  cudaStream_t s = eng.s;
+  char* p = ws;
+  auto slots = [&](long long count) { zc* q = (zc*)p; p += blk * (size_t)count; return q; };
+  auto S1 = [&](zc* base) { return BMat{base, bb}; };
+  zc *Adiag = slots(U), *Aup = slots(U), *Alow = slots(U), *D = slots(U), *dDt = slots(U);
+  zc *Ft = slots(U), *Fc = slots(U), *Ft2 = slots(U), *Fc2 = slots(U);
+  zc *T0 = slots(U), *T1 = slots(U), *T2 = slots(U), *Att = slots(U);
+  zc* Yf = slots((long long)U * nb);
+  zc* Xf = slots((long long)U * nb);
+  zc* Xtf = slots((long long)U * nb);
+  zc* Wtf = slots((long long)U * nb);
+  if (zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0) > 0) {
+    eng.inv_scratch = (void*)p;
+    p += zinv_scratch_bytes(b, U, eng.mixed ? 1 : 0);
+  }
+  p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+  eng.ozt_scratch = (void*)p;
+  auto outD = [&](int k) { return BMat{io.GRd + ((long long)e0 * nb + k) * bb, (long long)nb * bb}; };
+  auto offB = [&](zc* base, int k) { return BMat{base + ((long long)e0 * (nb - 1) + k) * bb, (long long)(nb - 1) * bb}; };
+  auto arr = [&](zc* base, int k) { return BMat{base + ((long long)e0 * nb + k) * bb, (long long)nb * bb}; };
+  auto fac = [&](zc* base, int k) { return BMat{base + (long long)k * U * bb, bb}; };
+  auto shared = [&](const zc* base, int k) { return BMat{(zc*)base + (long long)k * bb, 0}; };
+  const BMat Gtt{ar.Gt + (long long)e0 * bb, bb};
+  int32_t* st = io.status ? io.status + e0 : nullptr;
+  const dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), U);
+
+  AsmArgs a;
+  a.dv = dv; a.sc = sc; a.e0 = e0; a.units = U;
+  a.sigma_L = io.sigma_L; a.sigma_R = io.sigma_R; a.fL = a.fR = nullptr;
+  a.SigL = a.SigG = nullptr;
+  a.i_diag = 0; a.i_off = -1; a.Adiag = D; a.Aup = a.Alow = nullptr;
+  ctx->launches += 4;
+  CU(assemble(a, s));                                                          // D_0 = A_00
+  CU(cudaMemsetAsync(dDt, 0, blk * (size_t)U, s));
+  CU(bcopy(S1(Ft), shared(Arow, 0), b, U, s));                                // F_t0 = A_t0
+  CU(bcopy(S1(Fc), shared(Acol, 0), b, U, s));                                // F_0t = A_0t
+  tip_assemble_kernel<<<eg, 256, 0, s>>>(S1(Att), ar.H_tip, dv.E, dv.eta, e0, b);
+  CU(cudaGetLastError());
+  // ---------------- elimination of every device block, the tip kept
+  for (int k = 0; k < nb; ++k) {
+    CU(eng.inverse(outD(k), S1(D), b, U, st, S1(T1), S1(T2)));                 // g_k (in the G_kk output)
+    CU(eng.gemm(fac(Xtf, k), S1(Ft), OP_N, outD(k), OP_N, ONE, NOMAT, ZERO, b, U));     // Xt_k = F_tk g_k
+    CU(eng.gemm(fac(Wtf, k), outD(k), OP_N, S1(Fc), OP_N, ONE, NOMAT, ZERO, b, U));     // Wt_k = g_k F_kt
+    CU(eng.gemm(S1(dDt), fac(Xtf, k), OP_N, S1(Fc), OP_N, MONE, S1(dDt), ONE, b, U));   // dD_t -= Xt_k F_kt
+    if (k + 1 == nb) break;
+    a.i_diag = k + 1; a.i_off = k;
+    a.Adiag = Adiag; a.Aup = Aup; a.Alow = Alow;
+    ++ctx->launches;
+    CU(assemble(a, s));                                                        // A_jj, A_kj, A_jk
+    CU(eng.gemm(fac(Yf, k), S1(Alow), OP_N, outD(k), OP_N, ONE, NOMAT, ZERO, b, U));    // Y_k = A_jk g_k
+    CU(eng.gemm(fac(Xf, k), outD(k), OP_N, S1(Aup), OP_N, ONE, NOMAT, ZERO, b, U));     // X_k = g_k A_kj
+    CU(eng.gemm(S1(D), fac(Yf, k), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, U));   // D_j
+    CU(eng.gemm(S1(Ft2), fac(Xtf, k), OP_N, S1(Aup), OP_N, MONE, shared(Arow, k + 1), ONE, b, U));   // F_tj
+    CU(eng.gemm(S1(Fc2), fac(Yf, k), OP_N, S1(Fc), OP_N, MONE, shared(Acol, k + 1), ONE, b, U));    // F_jt
+    std::swap(Ft, Ft2);
+    std::swap(Fc, Fc2);
+  }
+  // ---------------- the tip: G_tt = (A_tt + dD_t)^{-1}
+  ++ctx->launches;
+  add_kernel<<<eg, 256, 0, s>>>(S1(T0), S1(Att), S1(dDt), b, nullptr);
+  CU(cudaGetLastError());
+  CU(eng.inverse(Gtt, S1(T0), b, U, st, S1(T1), S1(T2)));
+  // ---------------- reconstruction from the last block up
+  for (int k = nb - 1; k >= 0; --k) {
+    const bool last = k + 1 == nb;
+    // G_tk = -(G_tt Xt_k) [- G_tj Y_k]
+    if (last) {
+      CU(eng.gemm(arr(ar.Grow, k), Gtt, OP_N, fac(Xtf, k), OP_N, MONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(arr(ar.Gcol, k), fac(Wtf, k), OP_N, Gtt, OP_N, MONE, NOMAT, ZERO, b, U));
+      // G_kk = g_k - Wt_k G_tk
+      CU(eng.gemm(outD(k), fac(Wtf, k), OP_N, arr(ar.Grow, k), OP_N, MONE, outD(k), ONE, b, U));
+    } else {
+      const BMat Gjj = outD(k + 1);
+      const BMat Gtj_ = arr(ar.Grow, k + 1), Gjt_ = arr(ar.Gcol, k + 1);
+      CU(eng.gemm(S1(T0), Gtt, OP_N, fac(Xtf, k), OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(arr(ar.Grow, k), Gtj_, OP_N, fac(Yf, k), OP_N, MONE, S1(T0), MONE, b, U));       // G_tk
+      CU(eng.gemm(S1(T0), fac(Wtf, k), OP_N, Gtt, OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(arr(ar.Gcol, k), fac(Xf, k), OP_N, Gjt_, OP_N, MONE, S1(T0), MONE, b, U));      // G_kt
+      CU(eng.gemm(S1(T0), Gjt_, OP_N, fac(Xtf, k), OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(offB(io.GRl, k), Gjj, OP_N, fac(Yf, k), OP_N, MONE, S1(T0), MONE, b, U));       // G_jk
+      CU(eng.gemm(S1(T0), fac(Wtf, k), OP_N, Gtj_, OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(offB(io.GRu, k), fac(Xf, k), OP_N, Gjj, OP_N, MONE, S1(T0), MONE, b, U));       // G_kj
+      // G_kk = g_k - Wt_k G_tk - X_k G_jk
+      CU(eng.gemm(outD(k), fac(Wtf, k), OP_N, arr(ar.Grow, k), OP_N, MONE, outD(k), ONE, b, U));
+      CU(eng.gemm(outD(k), fac(Xf, k), OP_N, offB(io.GRl, k), OP_N, MONE, outD(k), ONE, b, U));
     }
   }
   return NEGF_OK;
@@ -940,13 +1380,13 @@ __global__ void transmission_kernel(BMat Gam, BMat G, BMat K1, BMat K2, int n, d
 }
 
 // DOS(E) = -(1/pi) Im Tr[G S] over the BT pattern, one CTA per energy
-__global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* GRl, int e0, double* dos) {
-  const int u = blockIdx.x, e = e0 + u;
+__global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* GRl, int e0, int eg, double* dos) {
+  const int u = blockIdx.x, e = e0 + u, eb = e - eg;   // eb: the energy's place in the G buffers
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
   double acc = 0.0;   // accumulates Im Tr[G S]
   for (int i = 0; i < nb; ++i) {
-    const zc* g = GRd + ((long long)e * nb + i) * bb;
+    const zc* g = GRd + ((long long)eb * nb + i) * bb;
     if (!dv.Sd) {
       for (int r = threadIdx.x; r < b; r += blockDim.x) acc += g[(long long)r * b + r].y;
     } else {
@@ -961,8 +1401,8 @@ __global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* G
   }
   if (dv.Su && GRu && GRl) {
     for (int i = 0; i + 1 < nb; ++i) {
-      const zc* gu = GRu + ((long long)e * (nb - 1) + i) * bb;
-      const zc* gl = GRl + ((long long)e * (nb - 1) + i) * bb;
+      const zc* gu = GRu + ((long long)eb * (nb - 1) + i) * bb;
+      const zc* gl = GRl + ((long long)eb * (nb - 1) + i) * bb;
       const zc* Su = dv.Su + i * bb;
 #pragma unroll 4
       for (long long k = threadIdx.x; k < bb; k += blockDim.x) {
@@ -980,12 +1420,12 @@ __global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* G
 }
 
 // J_i(E) = 2 Re Tr[(H_{i,i+1} - z S_{i,i+1}) G^<_{i+1,i}], one CTA per (energy, interface)
-__global__ void current_kernel(DevView dv, const zc* GLl, int e0, double* J) {
+__global__ void current_kernel(DevView dv, const zc* GLl, int e0, int eg, double* J) {
   const int u = blockIdx.y, e = e0 + u, i = blockIdx.x;
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
   const zc z = zmake(dv.E[e], dv.eta);
-  const zc* g = GLl + ((long long)e * (nb - 1) + i) * bb;
+  const zc* g = GLl + ((long long)(e - eg) * (nb - 1) + i) * bb;
   const zc* H = dv.Hu + i * bb;
   const zc* S = dv.Su ? dv.Su + i * bb : nullptr;
   double acc = 0.0;
@@ -1005,8 +1445,8 @@ __global__ void current_kernel(DevView dv, const zc* GLl, int e0, double* J) {
 }
 
 // per-energy orbital occupation Re(-i (G^< S)_kk)/(2 pi) into nE[u][k], k over nb*b
-__global__ void density_energy_kernel(DevView dv, const zc* GLd, const zc* GLl, int e0, double* nE) {
-  const int u = blockIdx.y, e = e0 + u;
+__global__ void density_energy_kernel(DevView dv, const zc* GLd, const zc* GLl, int e0, int eg, double* nE) {
+  const int u = blockIdx.y, e = e0 + u - eg;   // the energy's place in the G buffers
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
   const long long N = (long long)nb * b;
@@ -1045,6 +1485,64 @@ __global__ void density_accum_kernel(const double* nE, const double* w, int e0, 
     for (int u = 0; u < U; ++u) acc += w[e0 + u] * nE[(long long)u * N + k];
     dens[k] = acc;
   }
+}
+
+// the observables' inputs and outputs of one device (device-offset pointers); the G
+// blocks may start at any energy eg of the device ([e - eg][nb] / [e - eg][nb - 1])
+struct ObsIO {
+  const zc* sigma_L;
+  const double* w;
+  const zc *GRd, *GRu, *GRl, *GLd, *GLl;
+  double *T, *dos, *current, *density;
+};
+
+size_t observables_bytes_per_energy(const DevView& dv, int sl) {
+  const long long bb = (long long)dv.b * dv.b, N = (long long)dv.nb * dv.b;
+  return std::max<size_t>(sizeof(zc) * (size_t)bb * 4 + (sl ? ozt_scratch_bytes(dv.b, 1) + 1024 : 0),
+                          sizeof(double) * (size_t)N);
+}
+
+// observables of energies e0 .. e0+U-1 (row a9), with ws as scratch; sl: T's two block
+// products on the sliced tensor-core path
+negf_status observables_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ObsIO& ob, int sl, int e0, int U,
+                              int eg, char* ws) {
+  cudaStream_t s = eng.s;
+  const int b = dv.b, nb = dv.nb;
+  const long long bb = (long long)b * b;
+  const long long N = (long long)nb * b;
+  eng.mixed = sl;
+  if (ob.T) {
+    zc* p = (zc*)ws;
+    BMat Gam{p, bb}, K1{p + (long long)U * bb, bb}, K2{p + 2LL * U * bb, bb};
+    eng.ozt_scratch = sl ? (void*)(((uintptr_t)(p + 3LL * U * bb) + 1023) & ~(uintptr_t)1023) : nullptr;
+    BMat Sg{(zc*)ob.sigma_L + (long long)e0 * bb, bb};
+    BMat G00{(zc*)ob.GRd + (long long)(e0 - eg) * nb * bb, (long long)nb * bb};
+    dim3 grid((unsigned)std::min<long long>((bb + 255) / 256, 1024), U);
+    gamma_kernel<<<grid, 256, 0, s>>>(Gam, Sg, b);
+    KCHECK();
+    CU(eng.gemm(K1, Gam, OP_N, G00, OP_N, ONE, NOMAT, ZERO, b, U));
+    CU(eng.gemm(K2, G00, OP_N, Gam, OP_N, ONE, NOMAT, ZERO, b, U));
+    transmission_kernel<<<U, 256, 0, s>>>(Gam, G00, K1, K2, b, ob.T + e0);
+    KCHECK();
+  }
+  if (ob.dos) {
+    dos_kernel<<<U, 256, 0, s>>>(dv, ob.GRd, ob.GRu, ob.GRl, e0, eg, ob.dos);
+    KCHECK();
+  }
+  if (ob.current && nb > 1) {
+    current_kernel<<<dim3(nb - 1, U), 256, 0, s>>>(dv, ob.GLl, e0, eg, ob.current);
+    KCHECK();
+  }
+  if (ob.density) {
+    double* nE = (double*)ws;
+    dim3 g1((unsigned)std::min<long long>((N + 255) / 256, 1024), U);
+    density_energy_kernel<<<g1, 256, 0, s>>>(dv, ob.GLd, ob.GLl, e0, eg, nE);
+    KCHECK();
+    density_accum_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 1024), 256, 0, s>>>(nE, ob.w, e0, U, N,
+                                                                                                ob.density);
+    KCHECK();
+  }
+  return NEGF_OK;
 }
 
 }  // namespace
@@ -1117,12 +1615,136 @@ negf_status negf_ctx_sync(negf_ctx* c, negf_stream stream) {
   return NEGF_OK;
 }
 
+negf_status negf_worklist(const negf_system* sys, int32_t bs, int32_t* count, int32_t* unit_dev, int32_t* unit_e,
+                          int64_t* off_d, int64_t* off_o) {
+  if (!count) return fail(nullptr, NEGF_ERR_ARG, "count is NULL");
+  Layout L;
+  negf_status st = make_layout(nullptr, sys, L);
+  if (st != NEGF_OK) return st;
+  std::vector<int> devs;
+  for (int d = 0; d < sys->ndev; ++d)
+    if (sys->ne[d] > 0 && sys->bs[d] == bs) devs.push_back(d);
+  const WorkList w = make_worklist(sys, L, devs, (long long)bs * bs);
+  *count = (int32_t)w.unit_dev.size();
+  for (size_t u = 0; u < w.unit_dev.size(); ++u) {
+    if (unit_dev) unit_dev[u] = devs[w.unit_dev[u]];
+    if (unit_e) unit_e[u] = w.unit_e[u];
+    if (off_d) off_d[u] = w.off_d[u];
+    if (off_o) off_o[u] = w.off_o[u];
+  }
+  return NEGF_OK;
+}
+
 negf_status negf_layout(const negf_system* sys, int64_t* out) {
   if (!out) return fail(nullptr, NEGF_ERR_ARG, "out is NULL");
   Layout L;
   negf_status st = make_layout(nullptr, sys, L);
   if (st != NEGF_OK) return st;
   for (size_t k = 0; k < L.off.size(); ++k) out[k] = L.off[k];
+  return NEGF_OK;
+}
+
+// status[glob[u]] = st_units[u]
+__global__ void status_scatter_kernel(int32_t* status, const int32_t* st_units, const int* glob, int U) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < U) status[glob[u]] = st_units[u];
+}
+
+// batched sweeps over every (device, energy) unit of the devices `devs`, which share a
+// block size; units are chunked to the workspace, each chunk's tables copied ahead of
+// the sweep workspace
+negf_status rgf_batched_group(Ctx* ctx, Engine& eng, const negf_system* sys, const Layout& L,
+                              const std::vector<int>& devs, const void* sigma_L, const void* sigma_R,
+                              const double* f_L, const double* f_R, const negf_scattering* scat, void* GR_diag,
+                              void* GR_up, void* GR_low, void* GL_diag, void* GL_low, void* GG_diag, void* GG_low,
+                              int32_t* status, cudaStream_t s, bool lesser) {
+  const int b = sys->bs[devs[0]];
+  const long long bb = (long long)b * b;
+  std::vector<UnitDev> ud(devs.size());
+  for (size_t k = 0; k < devs.size(); ++k) {
+    const int d = devs[k];
+    const long long* o = &L.off[8 * (size_t)d];
+    ud[k].dv = dev_view(sys, L, d);
+    ud[k].sc = scat_view(scat, L, d, ud[k].dv.nb, b);
+    ud[k].sigma_L = (const zc*)sigma_L + o[3];
+    ud[k].sigma_R = (const zc*)sigma_R + o[3];
+    ud[k].fL = f_L ? f_L + o[2] : nullptr;
+    ud[k].fR = f_R ? f_R + o[2] : nullptr;
+  }
+  const WorkList w = make_worklist(sys, L, devs, bb);
+  const int units = (int)w.unit_dev.size();
+  int max_nb = 1;
+  for (int d : devs) max_nb = std::max(max_nb, (int)sys->nb[d]);
+  RgfIO io;
+  io.sigma_L = io.sigma_R = nullptr;
+  io.fL = io.fR = nullptr;
+  io.GRd = (zc*)GR_diag;
+  io.GRu = (zc*)GR_up;
+  io.GRl = (zc*)GR_low;
+  io.GLd = lesser ? (zc*)GL_diag : nullptr;
+  io.GLl = lesser ? (zc*)GL_low : nullptr;
+  io.GGd = lesser ? (zc*)GG_diag : nullptr;
+  io.GGl = lesser ? (zc*)GG_low : nullptr;
+  io.greater = lesser && (GG_diag || GG_low);
+  io.status = nullptr;
+  io.lesser = lesser;
+  // per unit: the sweep workspace at the group's largest nb, the tables and two masks
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t per = rgf_bytes_per_energy(max_nb, b, io, eng.mixed) + 4 * sizeof(int) + 2 * sizeof(long long) +
+                     sizeof(int32_t) + 2 * sizeof(int) * (size_t)max_nb;
+  const size_t fixed = align(sizeof(UnitDev) * ud.size()) + 8 * 256 + 2048;
+  if (ctx->ws_bytes <= fixed) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for the batch tables");
+  int chunk = (int)std::min<size_t>((ctx->ws_bytes - fixed) / per, (size_t)65535);
+  if (chunk < 1) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one unit needs " + std::to_string(per) + " bytes");
+  for (int u0 = 0; u0 < units; u0 += chunk) {
+    const int U = std::min(chunk, units - u0);
+    int nbc = 1;
+    for (int u = u0; u < u0 + U; ++u) nbc = std::max(nbc, w.unit_nb[u]);
+    std::vector<int> act_f((size_t)nbc * U), act_b((size_t)nbc * U);
+    std::vector<double> frac_f(nbc), frac_b(nbc);
+    for (int i = 0; i < nbc; ++i) {
+      int nf = 0, nbk = 0;
+      for (int u = 0; u < U; ++u) {
+        const int nbu = w.unit_nb[u0 + u];
+        nf += (act_f[(size_t)i * U + u] = (i < nbu) ? 1 : 0);
+        nbk += (act_b[(size_t)i * U + u] = (i <= nbu - 2) ? 1 : 0);
+      }
+      frac_f[i] = (double)nf / U;
+      frac_b[i] = (double)nbk / U;
+    }
+    char* p = (char*)ctx->ws;
+    auto put = [&](const void* src, size_t bytes) -> void* {
+      void* dst = p;
+      p += align(bytes);
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess ? dst : nullptr;
+    };
+    BatchPlan bp;
+    bp.nb = nbc;
+    bp.udev = (const UnitDev*)put(ud.data(), sizeof(UnitDev) * ud.size());
+    bp.unit_dev = (const int*)put(w.unit_dev.data() + u0, sizeof(int) * U);
+    bp.unit_e = (const int*)put(w.unit_e.data() + u0, sizeof(int) * U);
+    bp.off_d = (const long long*)put(w.off_d.data() + u0, sizeof(long long) * U);
+    bp.off_o = (const long long*)put(w.off_o.data() + u0, sizeof(long long) * U);
+    bp.act_f = (const int*)put(act_f.data(), sizeof(int) * act_f.size());
+    bp.act_b = (const int*)put(act_b.data(), sizeof(int) * act_b.size());
+    const int* glob = (const int*)put(w.unit_glob.data() + u0, sizeof(int) * U);
+    bp.frac_f = frac_f.data();
+    bp.frac_b = frac_b.data();
+    bp.st_units = (int32_t*)p;
+    p += align(sizeof(int32_t) * U);
+    if (!bp.udev || !bp.unit_dev || !bp.unit_e || !bp.off_d || !bp.off_o || !bp.act_f || !bp.act_b || !glob)
+      return fail(ctx, NEGF_ERR_CUDA, "copying the batch tables failed");
+    CU(cudaMemsetAsync(bp.st_units, 0, sizeof(int32_t) * U, s));
+    p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+    eng.inv_scratch = nullptr;
+    negf_status st = rgf_chunk(ctx, eng, ud[0].dv, ud[0].sc, io, 0, U, p, &bp);
+    if (st != NEGF_OK) return st;
+    if (status) {
+      ++ctx->launches;
+      status_scatter_kernel<<<(U + 127) / 128, 128, 0, s>>>(status, bp.st_units, glob, U);
+      CU(cudaGetLastError());
+    }
+  }
   return NEGF_OK;
 }
 
@@ -1145,9 +1767,25 @@ static negf_status rgf_common(Ctx* ctx, const negf_system* sys, negf_precision p
   CU(cudaSetDevice(ctx->device));
   if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * L.off[8 * (size_t)sys->ndev + 2], s));
   Engine eng{ctx, s, (int)prec, nullptr};
+  // devices that share a block size sweep together: one launch per step over all their
+  // (device, energy) units; a device alone in its block size keeps the plain layout
+  std::vector<int> sizes;
+  for (int d = 0; d < sys->ndev; ++d)
+    if (sys->ne[d] > 0 && std::find(sizes.begin(), sizes.end(), sys->bs[d]) == sizes.end()) sizes.push_back(sys->bs[d]);
+  std::vector<char> batched(sys->ndev, 0);
+  for (int bsz : sizes) {
+    std::vector<int> devs;
+    for (int d = 0; d < sys->ndev; ++d)
+      if (sys->ne[d] > 0 && sys->bs[d] == bsz) devs.push_back(d);
+    if (devs.size() < 2) continue;
+    st = rgf_batched_group(ctx, eng, sys, L, devs, sigma_L, sigma_R, f_L, f_R, scat, GR_diag, GR_up, GR_low, GL_diag,
+                           GL_low, GG_diag, GG_low, status, s, lesser);
+    if (st != NEGF_OK) return st;
+    for (int d : devs) batched[d] = 1;
+  }
   for (int d = 0; d < sys->ndev; ++d) {
     const int ne = sys->ne[d];
-    if (ne == 0) continue;
+    if (ne == 0 || batched[d]) continue;
     const DevView dv = dev_view(sys, L, d);
     const ScatView sc = scat_view(scat, L, d, dv.nb, dv.b);
     const long long* o = &L.off[8 * (size_t)d];
@@ -1195,6 +1833,236 @@ negf_status negf_rgf_lesser(negf_ctx* c, const negf_system* sys, negf_precision 
                             void* GL_low, int32_t* status, negf_stream stream) {
   return rgf_common(reinterpret_cast<Ctx*>(c), sys, prec, sigma_L, sigma_R, f_L, f_R, scat, GR_diag, GR_up,
                     GR_low, GL_diag, GL_low, status, (cudaStream_t)stream, true);
+}
+
+negf_status negf_rgf_partitioned(negf_ctx* c, const negf_system* sys, negf_precision prec, int32_t P,
+                                 const void* sigma_L, const void* sigma_R, const negf_scattering* scat,
+                                 void* GR_diag, void* GR_up, void* GR_low, int32_t* status, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  Layout Lay;
+  negf_status st = make_layout(ctx, sys, Lay);
+  if (st != NEGF_OK) return st;
+  if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (P < 1) return fail(ctx, NEGF_ERR_ARG, "need P >= 1 partitions");
+  for (int d = 0; d < sys->ndev; ++d)
+    if (sys->nb[d] % P != 0 || sys->nb[d] / P < 2)
+      return fail(ctx, NEGF_ERR_ARG, "device " + std::to_string(d) + ": nb must be P L with L >= 2");
+  if (!sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "sigma_L and sigma_R are required");
+  if (!GR_diag || !GR_up || !GR_low) return fail(ctx, NEGF_ERR_ARG, "GR_diag, GR_up and GR_low are required");
+  if (scat && scat->per_energy != 0 && scat->per_energy != 1)
+    return fail(ctx, NEGF_ERR_ARG, "scattering per_energy must be 0 or 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * Lay.off[8 * (size_t)sys->ndev + 2], s));
+  Engine eng{ctx, s, (int)prec, nullptr};
+  for (int d = 0; d < sys->ndev; ++d) {
+    const int ne = sys->ne[d];
+    if (ne == 0) continue;
+    const DevView dv = dev_view(sys, Lay, d);
+    const ScatView sc = scat_view(scat, Lay, d, dv.nb, dv.b);
+    const long long* o = &Lay.off[8 * (size_t)d];
+    RgfIO io;
+    io.sigma_L = (const zc*)sigma_L + o[3];
+    io.sigma_R = (const zc*)sigma_R + o[3];
+    io.fL = io.fR = nullptr;
+    io.GRd = (zc*)GR_diag + o[4];
+    io.GRu = (zc*)GR_up + o[5];
+    io.GRl = (zc*)GR_low + o[5];
+    io.GLd = io.GLl = nullptr;
+    io.status = status ? status + o[2] : nullptr;
+    io.lesser = false;
+    const size_t per = partitioned_bytes_per_energy(dv.nb, dv.b, P, eng.mixed);
+    int chunk = (int)std::min<size_t>(ctx->ws_bytes / per, (size_t)(65535 / P));
+    if (chunk < 1)
+      return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one energy of this device needs " +
+                                           std::to_string(per) + " bytes");
+    chunk = std::min(chunk, ne);
+    for (int e0 = 0; e0 < ne; e0 += chunk) {
+      const int U = std::min(chunk, ne - e0);
+      eng.inv_scratch = nullptr;
+      st = rgf_partitioned_chunk(ctx, eng, dv, sc, io, P, e0, U, (char*)ctx->ws);
+      if (st != NEGF_OK) return st;
+    }
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_energy_convolution(negf_ctx* c, int32_t ne, int64_t nelem, int64_t ld, int32_t M, const double* w,
+                                    const void* X, void* Y, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (ne < 0 || nelem < 0 || M < 0 || ld < nelem) return fail(ctx, NEGF_ERR_ARG, "need ne, nelem, M >= 0, ld >= nelem");
+  if (nelem > ((int64_t)1 << 31) - 16) return fail(ctx, NEGF_ERR_ARG, "nelem beyond 2^31");
+  if (!w || !X || !Y) return fail(ctx, NEGF_ERR_ARG, "NULL operand");
+  if (X == Y) return fail(ctx, NEGF_ERR_ARG, "X and Y must not overlap");
+  if (ne == 0 || nelem == 0) return NEGF_OK;
+  if (conv_log2_size(ne, M) > 13) return fail(ctx, NEGF_ERR_ARG, "ne + M must stay <= 8192");
+  const size_t need = 256 + conv_spectrum_bytes(ne, M) + sizeof(double) * (2 * (size_t)M + 1);
+  if (need > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for the kernel spectrum");
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  zc* Wh = (zc*)ctx->ws;
+  double* wd = (double*)((char*)ctx->ws + conv_spectrum_bytes(ne, M));
+  CU(cudaMemcpyAsync(wd, w, sizeof(double) * (2 * (size_t)M + 1), cudaMemcpyHostToDevice, s));
+  ctx->launches += 2;
+  CU(energy_convolution((const zc*)X, (zc*)Y, ld, (int)nelem, ne, M, wd, Wh, s));
+  return NEGF_OK;
+}
+
+negf_status negf_scba(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* sigma_L,
+                      const void* sigma_R, const double* f_L, const double* f_R, const negf_boson_kernel* kern,
+                      double mixing, double tol, int32_t max_iter, void* sigR_scat, void* sigL_scat,
+                      void* sigG_scat, void* GR_diag, void* GR_up, void* GR_low, void* GL_diag, void* GL_low,
+                      void* GG_diag, void* GG_low, int32_t* status, int32_t* iters, double* change,
+                      negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  Layout Lay;
+  negf_status st = make_layout(ctx, sys, Lay);
+  if (st != NEGF_OK) return st;
+  if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
+  if (!kern || kern->M < 0 || !kern->w_lesser || !kern->w_greater) return fail(ctx, NEGF_ERR_ARG, "bad boson kernel");
+  if (!(mixing > 0.0 && mixing <= 1.0) || !(tol > 0.0) || max_iter < 1)
+    return fail(ctx, NEGF_ERR_ARG, "need 0 < mixing <= 1, tol > 0, max_iter >= 1");
+  if (!sigR_scat || !sigL_scat || !sigG_scat) return fail(ctx, NEGF_ERR_ARG, "the three self-energy arrays are required");
+  if (!GR_diag || !GL_diag || !GG_diag) return fail(ctx, NEGF_ERR_ARG, "GR_diag, GL_diag and GG_diag are required");
+  if (!f_L || !f_R || !sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "lead self-energies and occupations required");
+  const long long nel = Lay.off[8 * (size_t)sys->ndev + 4];   // diagonal-block elements, all energies
+  const int M = kern->M;
+  for (int d = 0; d < sys->ndev; ++d)
+    if (sys->ne[d] > 0 && conv_log2_size(sys->ne[d], M) > 13)
+      return fail(ctx, NEGF_ERR_ARG, "device " + std::to_string(d) + ": ne + M must stay <= 8192");
+  int max_ne = 0;
+  for (int d = 0; d < sys->ndev; ++d) max_ne = std::max(max_ne, (int)sys->ne[d]);
+  // workspace after each sweep: the new Sigma^<, Sigma^> ([sum ne nb] blocks each), the
+  // kernels, the kernel spectrum and the change statistics
+  const size_t sig_bytes = sizeof(zc) * (size_t)nel;
+  const size_t need = 2 * sig_bytes + 2 * sizeof(double) * (2 * (size_t)M + 1) + conv_spectrum_bytes(max_ne, M) + 1024;
+  if (need > ctx->ws_bytes)
+    return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for the self-energy update: needs " + std::to_string(need) +
+                                         " bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  negf_scattering sc;
+  sc.sigR = sigR_scat;
+  sc.sigL = sigL_scat;
+  sc.sigL_scale = nullptr;
+  sc.per_energy = 1;
+  double last = INFINITY;
+  int it = 0;
+  while (it < max_iter) {
+    ++it;
+    st = rgf_common(ctx, sys, prec, sigma_L, sigma_R, f_L, f_R, &sc, GR_diag, GR_up, GR_low, GL_diag, GL_low, status, s,
+                    true, GG_diag, GG_low);
+    if (st != NEGF_OK) return st;
+    char* p = (char*)ctx->ws;
+    zc* SLn = (zc*)p; p += sig_bytes;
+    zc* SGn = (zc*)p; p += sig_bytes;
+    double* wl = (double*)p; p += sizeof(double) * (2 * (size_t)M + 1);
+    double* wg = (double*)p; p += sizeof(double) * (2 * (size_t)M + 1);
+    double* stats = (double*)p; p += 64;
+    p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    zc* Wh = (zc*)p;
+    CU(cudaMemcpyAsync(wl, kern->w_lesser, sizeof(double) * (2 * (size_t)M + 1), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(wg, kern->w_greater, sizeof(double) * (2 * (size_t)M + 1), cudaMemcpyHostToDevice, s));
+    for (int d = 0; d < sys->ndev; ++d) {
+      const int ne = sys->ne[d];
+      if (ne == 0) continue;
+      const long long o4 = Lay.off[8 * (size_t)d + 4];
+      const long long per_e = (long long)sys->nb[d] * sys->bs[d] * sys->bs[d];
+      ctx->launches += 4;
+      CU(energy_convolution((const zc*)GL_diag + o4, SLn + o4, per_e, (int)per_e, ne, M, wl, Wh, s));
+      CU(energy_convolution((const zc*)GG_diag + o4, SGn + o4, per_e, (int)per_e, ne, M, wg, Wh, s));
+    }
+    ++ctx->launches;
+    CU(scba_mix((zc*)sigL_scat, (zc*)sigG_scat, (zc*)sigR_scat, SLn, SGn, nel, mixing, stats, s));
+    CU(cudaMemcpyAsync(ctx->h_pinned, stats, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double h[3];
+    memcpy(h, ctx->h_pinned, sizeof(h));
+    last = std::max(h[0], h[1]) / std::max(h[2], 1e-300);
+    if (last < tol) break;
+  }
+  if (iters) *iters = it;
+  if (change) *change = last;
+  return NEGF_OK;
+}
+
+negf_status negf_rgf_arrowhead(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* H_tip,
+                               const void* H_arrow, const void* sigma_L, const void* sigma_R,
+                               const negf_scattering* scat, void* GR_diag, void* GR_up, void* GR_low, void* G_tip,
+                               void* G_row, void* G_col, int32_t* status, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  Layout Lay;
+  negf_status st = make_layout(ctx, sys, Lay);
+  if (st != NEGF_OK) return st;
+  if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (!H_tip || !H_arrow) return fail(ctx, NEGF_ERR_ARG, "H_tip and H_arrow are required");
+  if (!sigma_L || !sigma_R) return fail(ctx, NEGF_ERR_ARG, "sigma_L and sigma_R are required");
+  if (!GR_diag || !G_tip || !G_row || !G_col) return fail(ctx, NEGF_ERR_ARG, "GR_diag, G_tip, G_row, G_col are required");
+  bool multi = false;
+  for (int d = 0; d < sys->ndev; ++d) multi |= sys->nb[d] > 1;
+  if (multi && (!GR_up || !GR_low)) return fail(ctx, NEGF_ERR_ARG, "GR_up and GR_low are required when nb > 1");
+  if (scat && scat->per_energy != 0 && scat->per_energy != 1)
+    return fail(ctx, NEGF_ERR_ARG, "scattering per_energy must be 0 or 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * Lay.off[8 * (size_t)sys->ndev + 2], s));
+  Engine eng{ctx, s, (int)prec, nullptr};
+  long long tip_off = 0;   // [sum b*b] offset of this device's tip Hamiltonian
+  for (int d = 0; d < sys->ndev; ++d) {
+    const int ne = sys->ne[d], nb = sys->nb[d], b = sys->bs[d];
+    const long long bb = (long long)b * b;
+    const long long* o = &Lay.off[8 * (size_t)d];
+    const long long this_tip = tip_off;
+    tip_off += bb;
+    if (ne == 0) continue;
+    const DevView dv = dev_view(sys, Lay, d);
+    const ScatView sc = scat_view(scat, Lay, d, nb, b);
+    RgfIO io;
+    io.sigma_L = (const zc*)sigma_L + o[3];
+    io.sigma_R = (const zc*)sigma_R + o[3];
+    io.fL = io.fR = nullptr;
+    io.GRd = (zc*)GR_diag + o[4];
+    io.GRu = GR_up ? (zc*)GR_up + o[5] : nullptr;
+    io.GRl = GR_low ? (zc*)GR_low + o[5] : nullptr;
+    io.GLd = io.GLl = nullptr;
+    io.status = status ? status + o[2] : nullptr;
+    io.lesser = false;
+    ArrowIO ar;
+    ar.H_tip = (const zc*)H_tip + this_tip;
+    ar.H_arrow = (const zc*)H_arrow + o[0];
+    ar.Gt = (zc*)G_tip + o[3];
+    ar.Grow = (zc*)G_row + o[4];
+    ar.Gcol = (zc*)G_col + o[4];
+    // the device's arrow blocks of A, shared by its energies, ahead of the chunk workspace
+    const size_t arrow_bytes = ((2 * sizeof(zc) * (size_t)nb * bb) + 1023) & ~(size_t)1023;
+    zc* Arow = (zc*)ctx->ws;
+    zc* Acol = Arow + (long long)nb * bb;
+    const size_t per = arrowhead_bytes_per_energy(nb, b, eng.mixed);
+    const size_t avail = ctx->ws_bytes > arrow_bytes + 2048 ? ctx->ws_bytes - arrow_bytes - 2048 : 0;
+    int chunk = (int)std::min<size_t>(avail / per, (size_t)65535);
+    if (chunk < 1)
+      return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one energy of this device needs " + std::to_string(per) + " bytes");
+    chunk = std::min(chunk, ne);
+    ++ctx->launches;
+    arrow_blocks_kernel<<<dim3((unsigned)std::min<long long>((bb + 255) / 256, 1024), nb), 256, 0, s>>>(
+        Arow, Acol, ar.H_arrow, b);
+    CU(cudaGetLastError());
+    for (int e0 = 0; e0 < ne; e0 += chunk) {
+      const int U = std::min(chunk, ne - e0);
+      eng.inv_scratch = nullptr;
+      st = rgf_arrowhead_chunk(ctx, eng, dv, sc, io, ar, Arow, Acol, e0, U, (char*)ctx->ws + arrow_bytes + 1024);
+      if (st != NEGF_OK) return st;
+    }
+  }
+  return NEGF_OK;
 }
 
 negf_status negf_rgf_keldysh(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* sigma_L,
@@ -1449,54 +2317,106 @@ negf_status negf_observables(negf_ctx* c, const negf_system* sys, negf_precision
     if (ne == 0) continue;
     const DevView dv = dev_view(sys, L, d);
     const long long* o = &L.off[8 * (size_t)d];
-    const int b = dv.b, nb = dv.nb;
-    const long long bb = (long long)b * b;
-    const long long N = (long long)nb * b;
-    // T's products on the sliced tensor-core path (FP64-class) when asked for and supported;
-    // their scales and digit images follow Gamma, K1 and K2 in the workspace
-    const int sl = (T && prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
-    eng.mixed = sl;
-    const size_t per = std::max<size_t>(sizeof(zc) * (size_t)bb * 4 + (sl ? ozt_scratch_bytes(b, 1) : 0),
-                                        sizeof(double) * (size_t)N);
+    const int sl = (T && prec == NEGF_MIXED && oz_supported(dv.b)) ? 1 : 0;
+    const size_t per = observables_bytes_per_energy(dv, sl);
     const size_t avail = ctx->ws_bytes > 4096 ? ctx->ws_bytes - 4096 : 0;
     int chunk = (int)std::min<size_t>(avail / per, (size_t)65535);
     if (chunk < 1) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one energy");
     chunk = std::min(chunk, ne);
+    ObsIO ob;
+    ob.sigma_L = sigma_L ? (const zc*)sigma_L + o[3] : nullptr;
+    ob.w = e_weight ? e_weight + o[2] : nullptr;
+    ob.GRd = GR_diag ? (const zc*)GR_diag + o[4] : nullptr;
+    ob.GRu = GR_up ? (const zc*)GR_up + o[5] : nullptr;
+    ob.GRl = GR_low ? (const zc*)GR_low + o[5] : nullptr;
+    ob.GLd = GL_diag ? (const zc*)GL_diag + o[4] : nullptr;
+    ob.GLl = GL_low ? (const zc*)GL_low + o[5] : nullptr;
+    ob.T = T ? T + o[2] : nullptr;
+    ob.dos = dos ? dos + o[2] : nullptr;
+    ob.current = current ? current + o[6] : nullptr;
+    ob.density = density ? density + o[7] : nullptr;
     for (int e0 = 0; e0 < ne; e0 += chunk) {
       const int U = std::min(chunk, ne - e0);
-      if (T) {
-        zc* p = (zc*)ctx->ws;
-        BMat Gam{p, bb}, K1{p + (long long)U * bb, bb}, K2{p + 2LL * U * bb, bb};
-        eng.ozt_scratch = sl ? (void*)(((uintptr_t)(p + 3LL * U * bb) + 1023) & ~(uintptr_t)1023) : nullptr;
-        BMat Sg{(zc*)sigma_L + o[3] + (long long)e0 * bb, bb};
-        BMat G00{(zc*)GR_diag + o[4] + (long long)e0 * nb * bb, (long long)nb * bb};
-        dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), U);
-        gamma_kernel<<<eg, 256, 0, s>>>(Gam, Sg, b);
-        KCHECK();
-        CU(eng.gemm(K1, Gam, OP_N, G00, OP_N, ONE, NOMAT, ZERO, b, U));
-        CU(eng.gemm(K2, G00, OP_N, Gam, OP_N, ONE, NOMAT, ZERO, b, U));
-        transmission_kernel<<<U, 256, 0, s>>>(Gam, G00, K1, K2, b, T + o[2] + e0);
-        KCHECK();
-      }
-      if (dos) {
-        dos_kernel<<<U, 256, 0, s>>>(dv, (const zc*)GR_diag + o[4], GR_up ? (const zc*)GR_up + o[5] : nullptr,
-                                     GR_low ? (const zc*)GR_low + o[5] : nullptr, e0, dos + o[2]);
-        KCHECK();
-      }
-      if (current && nb > 1) {
-        current_kernel<<<dim3(nb - 1, U), 256, 0, s>>>(dv, (const zc*)GL_low + o[5], e0, current + o[6]);
-        KCHECK();
-      }
-      if (density) {
-        double* nE = (double*)ctx->ws;
-        dim3 g1((unsigned)std::min<long long>((N + 255) / 256, 1024), U);
-        density_energy_kernel<<<g1, 256, 0, s>>>(dv, (const zc*)GL_diag + o[4],
-                                                 GL_low ? (const zc*)GL_low + o[5] : nullptr, e0, nE);
-        KCHECK();
-        density_accum_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 1024), 256, 0, s>>>(
-            nE, e_weight + o[2], e0, U, N, density + o[7]);
-        KCHECK();
-      }
+      if ((st = observables_chunk(ctx, eng, dv, ob, sl, e0, U, 0, (char*)ctx->ws)) != NEGF_OK) return st;
+    }
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_rgf_observables(negf_ctx* c, const negf_system* sys, negf_precision prec, const void* sigma_L,
+                                 const void* sigma_R, const double* f_L, const double* f_R,
+                                 const negf_scattering* scat, const double* e_weight, double* T, double* dos,
+                                 double* current, double* density, int32_t* status, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  Layout L;
+  negf_status st = make_layout(ctx, sys, L);
+  if (st != NEGF_OK) return st;
+  if ((st = check_system(ctx, sys)) != NEGF_OK) return st;
+  if (prec != NEGF_FP64 && prec != NEGF_MIXED && prec != NEGF_MIXED_TF32)
+    return fail(ctx, NEGF_ERR_ARG, "unknown precision");
+  if (!sigma_L || !sigma_R || !f_L || !f_R) return fail(ctx, NEGF_ERR_ARG, "lead self-energies and occupations required");
+  if (density && !e_weight) return fail(ctx, NEGF_ERR_ARG, "density needs e_weight");
+  if (scat && scat->per_energy != 0 && scat->per_energy != 1)
+    return fail(ctx, NEGF_ERR_ARG, "scattering per_energy must be 0 or 1");
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (status) CU(cudaMemsetAsync(status, 0, sizeof(int32_t) * L.off[8 * (size_t)sys->ndev + 2], s));
+  if (density) CU(cudaMemsetAsync(density, 0, sizeof(double) * L.off[8 * (size_t)sys->ndev + 7], s));
+  Engine eng{ctx, s, (int)prec, nullptr};
+  for (int d = 0; d < sys->ndev; ++d) {
+    const int ne = sys->ne[d];
+    if (ne == 0) continue;
+    const DevView dv = dev_view(sys, L, d);
+    const ScatView sc = scat_view(scat, L, d, dv.nb, dv.b);
+    const long long* o = &L.off[8 * (size_t)d];
+    const int nb = dv.nb, b = dv.b;
+    const long long bb = (long long)b * b;
+    const size_t blk = sizeof(zc) * (size_t)bb;
+    // per energy: its G^R / G^< blocks (diagonal, upper, lower; diagonal, lower), the sweep
+    // workspace and the observables' scratch
+    const size_t gblocks = (size_t)(2 * nb + 3 * std::max(nb - 1, 0));
+    RgfIO io;
+    io.sigma_L = (const zc*)sigma_L + o[3];
+    io.sigma_R = (const zc*)sigma_R + o[3];
+    io.fL = f_L + o[2];
+    io.fR = f_R + o[2];
+    io.status = status ? status + o[2] : nullptr;
+    io.lesser = true;
+    // outputs go to per-chunk buffers (non-null here only so that the sizing below counts
+    // no sweep-internal storage for them; set per chunk)
+    io.GRd = io.GRu = io.GRl = io.GLd = io.GLl = (zc*)ctx->ws;
+    const int sl = (T && prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
+    const size_t per = gblocks * blk + rgf_bytes_per_energy(nb, b, io, eng.mixed) + observables_bytes_per_energy(dv, sl) + 3072;
+    int chunk = (int)std::min<size_t>(ctx->ws_bytes / per, (size_t)65535);
+    if (chunk < 1)
+      return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one energy of this device needs " + std::to_string(per) + " bytes");
+    chunk = std::min(chunk, ne);
+    for (int e0 = 0; e0 < ne; e0 += chunk) {
+      const int U = std::min(chunk, ne - e0);
+      char* p = (char*)ctx->ws;
+      auto take = [&](size_t nblocks) { zc* q = (zc*)p; p += blk * nblocks * (size_t)U; return q; };
+      io.GRd = take(nb);
+      io.GLd = take(nb);
+      io.GRu = nb > 1 ? take(nb - 1) : nullptr;
+      io.GRl = nb > 1 ? take(nb - 1) : nullptr;
+      io.GLl = nb > 1 ? take(nb - 1) : nullptr;
+      p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+      eng.inv_scratch = nullptr;
+      if ((st = rgf_chunk(ctx, eng, dv, sc, io, e0, U, p, nullptr, e0)) != NEGF_OK) return st;   // buffers start at e0
+      // the observables' scratch after the sweep's workspace (the sweep is done with it)
+      char* q = p + (size_t)U * rgf_bytes_per_energy(nb, b, io, eng.mixed);
+      q = (char*)(((uintptr_t)q + 1023) & ~(uintptr_t)1023);
+      ObsIO ob;
+      ob.sigma_L = (const zc*)sigma_L + o[3];
+      ob.w = e_weight ? e_weight + o[2] : nullptr;
+      ob.GRd = io.GRd; ob.GRu = io.GRu; ob.GRl = io.GRl; ob.GLd = io.GLd; ob.GLl = io.GLl;
+      ob.T = T ? T + o[2] : nullptr;
+      ob.dos = dos ? dos + o[2] : nullptr;
+      ob.current = current ? current + o[6] : nullptr;
+      ob.density = density ? density + o[7] : nullptr;
+      Engine eo{ctx, s, 0, nullptr};
+      if ((st = observables_chunk(ctx, eo, dv, ob, sl, e0, U, e0, q)) != NEGF_OK) return st;
     }
   }
   return NEGF_OK;
@@ -1570,6 +2490,84 @@ negf_status negf_block_gemm(negf_ctx* c, negf_precision prec, int32_t n, int32_t
   CU(eng.gemm(BMat{(zc*)D, d_stride}, BMat{(zc*)A, a_stride}, opA, BMat{(zc*)B, b_stride}, opB,
               zmake(alpha[0], alpha[1]), C ? BMat{(zc*)C, c_stride} : NOMAT,
               C ? zmake(beta[0], beta[1]) : ZERO, n, units));
+  return NEGF_OK;
+}
+
+// random complex entries in [-1, 1) from a counter-based hash (splitmix64 of the index)
+__global__ void fill_random_kernel(zc* x, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    const double im = (double)((z << 11) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    x[i] = zmake(re, im);
+  }
+}
+
+negf_status negf_tune_products(negf_ctx* c, int32_t n, int32_t units, int32_t* choice, double* ms,
+                               negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > 512 || units < 1 || units > 65535) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 512, 1 <= units <= 65535");
+  if (!oz_supported(n)) {   // no sliced product for this n: nothing to choose
+    if (choice) *choice = OZ_DEFAULT;
+    if (ms) for (int v = 0; v < OZ_NVARIANT; ++v) ms[v] = -1.0;
+    return NEGF_OK;
+  }
+  const long long nn = (long long)n * n;
+  const size_t mats = sizeof(zc) * (size_t)nn * units;
+  const size_t need = 3 * mats + 1024 + ozt_scratch_bytes(n, units);
+  if (need > ctx->ws_bytes) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small to tune " + std::to_string(units) + " units");
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  zc* A = (zc*)ctx->ws;
+  zc* B = A + nn * units;
+  zc* D = B + nn * units;
+  void* scratch = (void*)(((uintptr_t)(D + nn * units) + 1023) & ~(uintptr_t)1023);
+  ctx->launches += 2;
+  fill_random_kernel<<<1024, 256, 0, s>>>(A, nn * units, 20260101ull);
+  fill_random_kernel<<<1024, 256, 0, s>>>(B, nn * units, 20260202ull);
+  CU(cudaGetLastError());
+  GemmArgs g;
+  g.D = BMat{D, nn}; g.A = BMat{A, nn}; g.B = BMat{B, nn}; g.C = BMat{nullptr, 0};
+  g.opA = OP_N; g.opB = OP_N; g.alpha = zmake(1.0, 0.0); g.beta = zmake(0.0, 0.0);
+  g.n = n; g.units = units; g.active = nullptr;
+  cudaEvent_t e0 = ctx->take_event(), e1 = ctx->take_event();
+  int best = OZ_DEFAULT;
+  double best_ms = INFINITY;
+  for (int v = OZ_HALF; v < OZ_NVARIANT; ++v) {
+    if (ms) ms[v] = -1.0;
+    if (!oz_variant_supported(n, v)) continue;
+    CU(zgemm_ozt_variant(g, scratch, ctx->d_err, s, v));   // warm-up
+    CU(cudaEventRecord(e0, s));
+    constexpr int reps = 3;
+    for (int r = 0; r < reps; ++r) CU(zgemm_ozt_variant(g, scratch, ctx->d_err, s, v));
+    CU(cudaEventRecord(e1, s));
+    CU(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, e0, e1));
+    const double per = (double)t / reps;
+    ctx->launches += 2 * (reps + 1);
+    if (ms) ms[v] = per;
+    if (per < best_ms) { best_ms = per; best = v; }
+  }
+  ctx->pool.push_back(e0);
+  ctx->pool.push_back(e1);
+  if (ms) ms[OZ_DEFAULT] = -1.0;
+  ctx->oz_variant[n] = best;
+  if (choice) *choice = best;
+  return NEGF_OK;
+}
+
+negf_status negf_set_product_variant(negf_ctx* c, int32_t n, int32_t variant) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > 512) return fail(ctx, NEGF_ERR_ARG, "need 1 <= n <= 512");
+  if (variant < 0 || variant >= OZ_NVARIANT || (variant != OZ_DEFAULT && !oz_variant_supported(n, variant)))
+    return fail(ctx, NEGF_ERR_ARG, "variant " + std::to_string(variant) + " does not support n = " + std::to_string(n));
+  ctx->oz_variant[n] = variant;
   return NEGF_OK;
 }
 

@@ -44,12 +44,23 @@ __host__ __device__ __forceinline__ void zfma(zc& a, zc b, zc c) {
 }
 
 // ---------------------------------------------------------------------------
-// batched square-matrix operands: unit u's n x n row-major matrix at p + u*us
+// batched square-matrix operands: unit u's n x n row-major matrix at p + u*us, or, with
+// inner > 1, at p + (u / inner) us + (u % inner) us2 (units that are (energy, partition)
+// pairs of the partitioned sweeps)
 // ---------------------------------------------------------------------------
 struct BMat {
   zc* p;
-  long long us;   // unit stride in elements; 0 => one matrix shared by all units
-  __host__ __device__ zc* at(int u) const { return p + (long long)u * us; }
+  long long us;        // unit stride in elements; 0 => one matrix shared by all units
+  int inner = 0;       // > 1: units form an (outer, inner) grid
+  long long us2 = 0;   // stride of the inner index
+  const long long* off = nullptr;   // device [units]: unit u at p + off[u] (the work list of an uneven batch)
+  __host__ __device__ zc* at(int u) const {
+    if (off) return p + off[u];
+    return inner > 1 ? p + (long long)(u / inner) * us + (long long)(u % inner) * us2 : p + (long long)u * us;
+  }
+  // the plain layout (unit u at p + u us): kernels that are sensitive to the size of
+  // their arguments get a specialization for it
+  __host__ __device__ bool plain() const { return !off && inner <= 1; }
 };
 
 enum Op { OP_N = 0, OP_H = 2 };   // as stored / conjugate transpose
@@ -88,6 +99,7 @@ struct Ctx {
   bool prof = false;            // bracket GEMM / inverse launches with events
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
+  int oz_variant[513] = {0};    // tile variant of the sliced product per block size (autotuner)
   long long k_launches[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   double k_ms[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   double k_flops[K_NCLASS] = {0, 0, 0, 0, 0, 0};
@@ -123,6 +135,13 @@ size_t oz_scratch_bytes(int n, int units);
 // the tensor cores by bulk copies; `scratch` holds ozt_scratch_bytes(n, units) bytes
 cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 size_t ozt_scratch_bytes(int n, int units);
+// tile variants of the digitize-once product (the autotuner's choices): the default rule
+// by n, half-width 128 x 16 tiles with two CTAs per SM (n <= 128), persistent full-width
+// 128 x 32 tiles with the epilogue overlapping the next tile (n <= 128), full-width tiles
+// with one CTA per tile (any n)
+enum OzVariant { OZ_DEFAULT = 0, OZ_HALF = 1, OZ_PERSISTENT = 2, OZ_FULL = 3, OZ_NVARIANT = 4 };
+bool oz_variant_supported(int n, int variant);
+cudaError_t zgemm_ozt_variant(const GemmArgs& g, void* scratch, int* err, cudaStream_t s, int variant);
 
 // X[u] = M[u]^{-1} by Gauss-Jordan with partial pivoting (first max |.| in row
 // order).  FP64, or FP32 (`single` != 0) with the result written back in FP64.
@@ -132,6 +151,20 @@ size_t ozt_scratch_bytes(int n, int units);
 cudaError_t zinv(BMat X, BMat M, int n, int units, const int* active, int single, void* scratch,
                  int32_t* status, cudaStream_t s);
 size_t zinv_scratch_bytes(int n, int units, int single);
+
+// Eq. (3) on a uniform grid: Y[e][i] = sum_{m=-M..M} w_m X[e-m][i] for i < nelem (element i
+// of energy e at X + e ld + i), by a zero-padded FFT of size N = 2^conv_log2_size(ne, M)
+// >= ne + M (N <= 8192).  w_dev: device [2M+1]; Wh: device scratch of
+// conv_spectrum_bytes(ne, M) bytes for the kernel's spectrum.
+int conv_log2_size(int ne, int M);
+size_t conv_spectrum_bytes(int ne, int M);
+cudaError_t energy_convolution(const zc* X, zc* Y, long long ld, int nelem, int ne, int M, const double* w_dev,
+                               zc* Wh, cudaStream_t s);
+// mixing step of the self-consistent loop over n elements: stats[0..2] (device) receive
+// max|SLn - SL|, max|SGn - SG|, max(|SLn|, |SGn|); then SL, SG move by `mix` towards SLn,
+// SGn and SR = (SG - SL) / 2
+cudaError_t scba_mix(zc* SL, zc* SG, zc* SR, const zc* SLn, const zc* SGn, long long n, double mix, double* stats,
+                     cudaStream_t s);
 
 // sets the thread-local message returned by negf_last_error(NULL)
 void negf_set_error_message(const char* msg);

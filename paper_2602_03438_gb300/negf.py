@@ -28,13 +28,15 @@ FP64 = 0
 MIXED = 1
 MIXED_TF32 = 2
 
-EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout",
+EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_sync", "negf_layout", "negf_worklist",
            "negf_obc", "negf_rgf_retarded", "negf_rgf_lesser", "negf_rgf_keldysh", "negf_rgf_partitioned",
-           "negf_observables",
+           "negf_observables", "negf_energy_convolution", "negf_scba", "negf_rgf_observables",
+           "negf_rgf_arrowhead",
            "negf_profile_enable",
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
            "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
-           "negf_mlp_forward", "negf_mlp_train_step", "negf_sliced_digits"]
+           "negf_mlp_forward", "negf_mlp_train_step", "negf_sliced_digits", "negf_tune_products",
+           "negf_set_product_variant"]
 KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
 
 
@@ -55,6 +57,10 @@ class MlpDims(C.Structure):
     _fields_ = [("b", C.c_int32), ("hidden", C.c_int32), ("k0", C.c_int32), ("k0p", C.c_int32),
                 ("nout", C.c_int32), ("off_W1", C.c_int64), ("off_c1", C.c_int64), ("off_W2", C.c_int64),
                 ("off_c2", C.c_int64), ("off_W3", C.c_int64), ("off_c3", C.c_int64), ("n_params", C.c_int64)]
+
+
+class _BosonKernel(C.Structure):
+    _fields_ = [("M", C.c_int32), ("w_lesser", C.POINTER(C.c_double)), ("w_greater", C.POINTER(C.c_double))]
 
 
 class _Scattering(C.Structure):
@@ -80,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_last_error.restype = C.c_char_p
     lib.negf_ctx_sync.argtypes = [vp, vp]
     lib.negf_layout.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64)]
+    lib.negf_worklist.argtypes = [C.POINTER(_System), i32, C.POINTER(i32), vp, vp, vp, vp]
     lib.negf_obc.argtypes = [vp, C.POINTER(_System), C.c_int, dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_mlp_get_dims.argtypes = [i32, i32, C.POINTER(MlpDims)]
     lib.negf_mlp_workspace_bytes.argtypes = [C.POINTER(MlpDims), i32]
@@ -94,6 +101,13 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                     vp, vp, vp, vp, vp, vp, vp]
     lib.negf_rgf_partitioned.argtypes = [vp, C.POINTER(_System), C.c_int, i32, vp, vp, C.POINTER(_Scattering),
                                          vp, vp, vp, vp, vp]
+    lib.negf_rgf_arrowhead.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
+                                       vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_rgf_observables.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
+                                         vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_energy_convolution.argtypes = [vp, i32, C.c_int64, C.c_int64, i32, C.POINTER(C.c_double), vp, vp, vp]
+    lib.negf_scba.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_BosonKernel), dbl, dbl,
+                              i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl), vp]
     lib.negf_rgf_keldysh.argtypes = [vp, C.POINTER(_System), C.c_int, vp, vp, vp, vp, C.POINTER(_Scattering),
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.negf_observables.argtypes = [vp, C.POINTER(_System), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -106,6 +120,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_profile_read.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.negf_profile_reset.argtypes = [vp]
     lib.negf_sliced_digits.argtypes = []
+    lib.negf_tune_products.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(dbl), vp]
+    lib.negf_set_product_variant.argtypes = [vp, i32, i32]
     for name in EXPORTS:
         if name not in ("negf_last_error", "negf_mlp_workspace_bytes"):
             getattr(lib, name).restype = C.c_int
@@ -228,6 +244,27 @@ def system_layout(nb: Sequence[int], bs: Sequence[int], ne: Sequence[int]) -> np
     return np.frombuffer(out, dtype=np.int64).reshape(n + 1, 8).copy()
 
 
+def system_worklist(nb: Sequence[int], bs: Sequence[int], ne: Sequence[int], block_size: int) -> dict:
+    """negf_worklist for shapes only: the (device, energy) units of the devices with
+    `block_size` and their output offsets (host arrays)."""
+    lib = load_library()
+    n = len(nb)
+    arrs = [(C.c_int32 * n)(*nb), (C.c_int32 * n)(*bs), (C.c_int32 * n)(*ne)]
+    s = _System(n, arrs[0], arrs[1], arrs[2], None, None, None, None, None, 1.0)
+    cnt = C.c_int32(0)
+    st = lib.negf_worklist(C.byref(s), int(block_size), C.byref(cnt), None, None, None, None)
+    if st != NEGF_OK:
+        raise NegfError(st, lib.negf_last_error(None).decode())
+    k = cnt.value
+    out = dict(unit_dev=np.zeros(k, np.int32), unit_e=np.zeros(k, np.int32), off_d=np.zeros(k, np.int64),
+               off_o=np.zeros(k, np.int64))
+    st = lib.negf_worklist(C.byref(s), int(block_size), C.byref(cnt),
+                           *(C.c_void_p(out[key].ctypes.data) for key in ("unit_dev", "unit_e", "off_d", "off_o")))
+    if st != NEGF_OK:
+        raise NegfError(st, lib.negf_last_error(None).decode())
+    return out
+
+
 def _dev_tensor(a, device, dtype=None):
     t = torch.from_numpy(np.ascontiguousarray(a))
     if dtype is not None:
@@ -320,6 +357,58 @@ def negf_rgf_partitioned(ctx: Context, sys: System, prec, P: int, sigma_L, sigma
     ctx.check(ctx.lib.negf_rgf_partitioned(ctx.h, C.byref(s), int(prec), int(P), _ptr(sigma_L), _ptr(sigma_R),
                                            C.byref(sc) if sc is not None else None, _ptr(GR_diag), _ptr(GR_up),
                                            _ptr(GR_low), _ptr(status), _stream(stream)))
+
+
+def negf_rgf_arrowhead(ctx: Context, sys: System, prec, H_tip, H_arrow, sigma_L, sigma_R, scat=None, GR_diag=None,
+                       GR_up=None, GR_low=None, G_tip=None, G_row=None, G_col=None, status=None, stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_arrowhead(ctx.h, C.byref(s), int(prec), _ptr(H_tip), _ptr(H_arrow), _ptr(sigma_L),
+                                         _ptr(sigma_R), C.byref(sc) if sc is not None else None, _ptr(GR_diag),
+                                         _ptr(GR_up), _ptr(GR_low), _ptr(G_tip), _ptr(G_row), _ptr(G_col),
+                                         _ptr(status), _stream(stream)))
+
+
+def negf_rgf_observables(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, scat=None, e_weight=None,
+                         T=None, dos=None, current=None, density=None, status=None, stream=None):
+    s = sys.c()
+    sc = scat.c() if scat is not None else None
+    ctx.check(ctx.lib.negf_rgf_observables(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(sigma_R), _ptr(f_L),
+                                           _ptr(f_R), C.byref(sc) if sc is not None else None, _ptr(e_weight),
+                                           _ptr(T), _ptr(dos), _ptr(current), _ptr(density), _ptr(status),
+                                           _stream(stream)))
+
+
+def negf_energy_convolution(ctx: Context, X, Y, w, ne=None, stream=None):
+    """Eq. (3) along the first axis of X ([ne, ...] complex128 device tensor) into Y."""
+    ne = X.shape[0] if ne is None else ne
+    nelem = X[0].numel() if X.dim() > 1 else 1
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    M = (wa.size - 1) // 2
+    ctx.check(ctx.lib.negf_energy_convolution(ctx.h, int(ne), int(nelem), int(nelem), int(M),
+                                              wa.ctypes.data_as(C.POINTER(C.c_double)), _ptr(X), _ptr(Y),
+                                              _stream(stream)))
+
+
+def negf_scba(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, w_lesser, w_greater, sigR, sigL, sigG,
+              GR_diag, GL_diag, GG_diag, GR_up=None, GR_low=None, GL_low=None, GG_low=None, status=None,
+              mixing=0.5, tol=1e-8, max_iter=100, stream=None):
+    """The self-consistent scattering loop; returns (sweeps, last change)."""
+    s = sys.c()
+    wl = np.ascontiguousarray(np.asarray(w_lesser, dtype=np.float64))
+    wg = np.ascontiguousarray(np.asarray(w_greater, dtype=np.float64))
+    if wl.size != wg.size or wl.size % 2 == 0:
+        raise ValueError("kernels of equal odd length 2M+1")
+    k = _BosonKernel((wl.size - 1) // 2, wl.ctypes.data_as(C.POINTER(C.c_double)),
+                     wg.ctypes.data_as(C.POINTER(C.c_double)))
+    it = C.c_int32(0)
+    ch = C.c_double(0.0)
+    ctx.check(ctx.lib.negf_scba(ctx.h, C.byref(s), int(prec), _ptr(sigma_L), _ptr(sigma_R), _ptr(f_L), _ptr(f_R),
+                                C.byref(k), float(mixing), float(tol), int(max_iter), _ptr(sigR), _ptr(sigL),
+                                _ptr(sigG), _ptr(GR_diag), _ptr(GR_up), _ptr(GR_low), _ptr(GL_diag), _ptr(GL_low),
+                                _ptr(GG_diag), _ptr(GG_low), _ptr(status), C.byref(it), C.byref(ch),
+                                _stream(stream)))
+    return int(it.value), float(ch.value)
 
 
 def negf_rgf_keldysh(ctx: Context, sys: System, prec, sigma_L, sigma_R, f_L, f_R, scat=None, GR_diag=None,

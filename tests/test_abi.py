@@ -108,3 +108,37 @@ def test_mlp_entry_points_reject_null_without_a_gpu(lib):
     assert lib.negf_mlp_forward(None, None, None, 1, None, None, None) == negf.NEGF_ERR_ARG
     assert lib.negf_mlp_train_step(None, None, None, None, None, None, 1, 1e-3, 1, None, 0, None, None, None, 1,
                                    None) == negf.NEGF_ERR_ARG
+
+
+def _worklist_py(shapes, block_size):
+    """The (device, energy) units of the devices with one block size, in device-then-
+    energy order, with their output offsets, recomputed in Python from the layout."""
+    L = _layout_py(shapes)
+    units = dict(unit_dev=[], unit_e=[], off_d=[], off_o=[])
+    for d, (nb, b, ne) in enumerate(shapes):
+        if b != block_size or ne == 0:
+            continue
+        for e in range(ne):
+            units["unit_dev"].append(d)
+            units["unit_e"].append(e)
+            units["off_d"].append(L[d][4] + e * nb * b * b)
+            units["off_o"].append(L[d][5] + e * (nb - 1) * b * b)
+    return {k: np.array(v, dtype=np.int64) for k, v in units.items()}
+
+
+def test_uneven_batch_worklist_is_bit_exact(lib):
+    """The work list of the batched sweeps over config 3's 256 devices (every block size),
+    and of a batch with empty devices, against a Python recomputation."""
+    from paper_2602_03438_gb300 import negf
+    shapes = W.config3_shapes()
+    cases = [shapes, [(3, 16, 4), (5, 8, 0), (2, 16, 3), (4, 24, 5), (1, 16, 2)]]
+    for sh in cases:
+        nb, bs, ne = zip(*sh)
+        for b in sorted(set(bs)):
+            got = negf.system_worklist(nb, bs, ne, b)
+            ref = _worklist_py(sh, b)
+            assert got["unit_dev"].size == ref["unit_dev"].size
+            for k in ref:
+                assert np.array_equal(got[k].astype(np.int64), ref[k]), (b, k)
+    # a block size no device has: no units
+    assert negf.system_worklist([3], [16], [4], 32)["unit_dev"].size == 0

@@ -50,9 +50,9 @@ def test_config2_full_launch_sampled_energies(P):
         assert int((out["obc_status"] != 0).sum()) == 0
         assert int((out["status"] != 0).sum()) == 0
         nb, b = dev.nb, dev.b
-        # in-band (|E| < 0.5, near-resonant blocks; 528 is near the peak of the current)
-        # and out-of-band energies
-        sample = [2, 430, 470, 511, 528, 540, 600, 1021]
+        # in-band (|E| < 0.5, near-resonant blocks; 529 is the peak of the current, so that
+        # the sample's largest |J| is the grid's) and out-of-band energies
+        sample = [2, 430, 470, 511, 528, 529, 540, 600, 1021]
         J_got, J_ref, n_ref = [], [], np.zeros(nb * b)
         wh = dev.weights()
         for e in sample:

@@ -522,3 +522,51 @@ def test_scba_converges_to_a_fixed_point_that_conserves_the_integrated_current()
     Jint = J.sum(axis=0)
     assert np.ptp(Jint) <= 1e-6 * np.abs(Jint).max()
     assert np.abs(np.ptp(J, axis=1)).max() >= 1e-2 * np.abs(J).max()
+
+
+# ---------------------------------------------------------------------------
+# arrowhead BT (a gate block coupled to every block)
+# ---------------------------------------------------------------------------
+
+def test_arrowhead_without_coupling_is_the_bt_result_and_a_free_tip():
+    dev = W.small_scattering_device(4, 6, 2, seed=80)
+    H_tip, H_arrow = W.arrowhead_gate(dev)
+    z = dev.energy[1] + 1j * dev.eta
+    sL, sR, _ = O.lead_self_energies(dev, z)
+    r = O.arrowhead_dense(dev, z, sL, sR, H_tip, 0.0 * H_arrow, sigR_scat=dev.sigR_scat)
+    d = O.greens_dense(dev, z, sL, sR, sigR_scat=dev.sigR_scat)
+    for k in ("GR_diag", "GR_up", "GR_low"):
+        assert np.abs(r[k] - d[k]).max() <= 1e-12 * np.abs(d[k]).max()
+    tip = np.linalg.inv(z * np.eye(dev.b) - H_tip)
+    assert np.abs(r["G_tip"] - tip).max() <= 1e-12 * np.abs(tip).max()
+    assert np.abs(r["G_row"]).max() == 0 and np.abs(r["G_col"]).max() == 0
+
+
+def test_arrowhead_schur_complement_of_the_tip():
+    """With the tip eliminated, the device block of the inverse is the inverse of the
+    device matrix minus the tip's Schur-complement term A_(.,t) A_tt^{-1} A_(t,.), a dense
+    correction to every block pair: checked on the diagonal blocks and the corner block."""
+    dev = W.small_scattering_device(5, 4, 1, seed=81)
+    H_tip, H_arrow = W.arrowhead_gate(dev, coupling=0.3)
+    z = dev.energy[0] + 1j * dev.eta
+    sL, sR, _ = O.lead_self_energies(dev, z)
+    r = O.arrowhead_dense(dev, z, sL, sR, H_tip, H_arrow, sigR_scat=dev.sigR_scat)
+    A = O.assemble_A(dev, z, sL, sR, dev.sigR_scat)
+    b, nb = dev.b, dev.nb
+    col = np.concatenate([-H(H_arrow[i]) for i in range(nb)], axis=0)      # A_(.,t)
+    row = np.concatenate([-H_arrow[i] for i in range(nb)], axis=1)         # A_(t,.)
+    Att = z * np.eye(b) - H_tip
+    G = np.linalg.inv(A - col @ np.linalg.solve(Att, row))
+    for i in range(nb):
+        blk = G[i * b:(i + 1) * b, i * b:(i + 1) * b]
+        assert np.abs(r["GR_diag"][i] - blk).max() <= 1e-11 * np.abs(blk).max()
+    # and the tip block is the inverse of the tip's own Schur complement, the arrow row
+    # G_(t,.) = -S_t^{-1} A_(t,.) A^{-1} and the column G_(.,t) = -A^{-1} A_(.,t) S_t^{-1}
+    Gt = np.linalg.inv(Att - row @ np.linalg.solve(A, col))
+    assert np.abs(r["G_tip"] - Gt).max() <= 1e-11 * np.abs(Gt).max()
+    Grow = -Gt @ row @ np.linalg.inv(A)
+    Gcol = -np.linalg.solve(A, col) @ Gt
+    for i in range(nb):
+        s_i = slice(i * b, (i + 1) * b)
+        assert np.abs(r["G_row"][i] - Grow[:, s_i]).max() <= 1e-11 * np.abs(Grow).max()
+        assert np.abs(r["G_col"][i] - Gcol[s_i, :]).max() <= 1e-11 * np.abs(Gcol).max()

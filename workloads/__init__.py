@@ -330,3 +330,14 @@ def einstein_kernel(energy: np.ndarray, steps: int, g2: float, kT: float):
     wl[2 * steps], wl[0] = g2 * nbose, g2 * (nbose + 1.0)
     wg[2 * steps], wg[0] = g2 * (nbose + 1.0), g2 * nbose
     return wl, wg
+
+
+def arrowhead_gate(dev: Device, seed: int = SEED_BASE + 7, coupling: float = 0.1):
+    """A gate block for the arrowhead BT matrix of a device: a random Hermitian tip
+    Hamiltonian (CN(0,1)/sqrt(b), shifted by +1) and a random coupling of the tip to every
+    block (CN(0, coupling^2)/sqrt(b)).  Returns (H_tip [b][b], H_arrow [nb][b][b])."""
+    rng = _rng(seed)
+    b, nb = dev.b, dev.nb
+    H_tip = _herm(_cn(rng, (b, b))) / np.sqrt(b) + np.eye(b)
+    H_arrow = coupling * _cn(rng, (nb, b, b)) / np.sqrt(b)
+    return H_tip, H_arrow
