@@ -1008,15 +1008,25 @@ struct LeadArgs {
   DevView dv;
   int e0, U;
   zc *a00, *al0, *be0, *eps, *epss, *al, *be;   // slot bases, unit stride b*b, 2U units
+  // units of a batched group: energy unit_e[k] of device udev[unit_dev[k]] (then dv and
+  // e0 are unused)
+  const UnitDev* udev = nullptr;
+  const int* unit_dev = nullptr;
+  const int* unit_e = nullptr;
 };
 
 // unit u < U: left lead of energy e0+u; u >= U: right lead of energy e0+u-U
 __global__ void lead_init_kernel(LeadArgs a) {
   const int u = blockIdx.y;
+  const bool left = u < a.U;
+  const int k = left ? u : u - a.U;   // the energy unit
+  int e = a.e0 + k;
+  if (a.udev) {
+    a.dv = a.udev[a.unit_dev[k]].dv;
+    e = a.unit_e[k];
+  }
   const int b = a.dv.b, nb = a.dv.nb;
   const long long bb = (long long)b * b;
-  const bool left = u < a.U;
-  const int e = a.e0 + (left ? u : u - a.U);
   const zc z = zmake(a.dv.E[e], a.dv.eta);
   const int cd = left ? 0 : nb - 1;   // lead cell copies this device block
   const int cu = left ? 0 : nb - 2;   // ... and this hop
@@ -1222,14 +1232,16 @@ __global__ void newton_take_kernel(BMat g, BMat gn, int n, double* res, const do
 }
 
 // g[u] = the guess of its side (left units u < U, right units u >= U), warm[u] = 1 when given
-__global__ void guess_init_kernel(BMat g, const zc* g0L, const zc* g0R, int U, int n, int* warm) {
+__global__ void guess_init_kernel(BMat g, const zc* g0L, const zc* g0R, int U, int n, int* warm,
+                                  const long long* off = nullptr) {
   const int u = blockIdx.y;
   const bool left = u < U;
   const zc* src = left ? g0L : g0R;
   if (blockIdx.x == 0 && threadIdx.x == 0) warm[u] = src ? 1 : 0;
   if (!src) return;
   const long long nn = (long long)n * n;
-  src += (long long)(left ? u : u - U) * nn;
+  const int k = left ? u : u - U;
+  src += off ? off[k] : (long long)k * nn;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
     g.at(u)[i] = src[i];
 }
@@ -1315,19 +1327,21 @@ __global__ void set_need_kernel(const double* res, int* need, int units, double 
 }
 
 __global__ void obc_finish_kernel(const int* done, const double* res, const int* iters, const int* nsteps, int U,
-                                  int32_t* status, int32_t* iters_out, int32_t* newton_out, double accept) {
+                                  int32_t* status, int32_t* iters_out, int32_t* newton_out, double accept,
+                                  const int* glob = nullptr) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= U) return;
+  const int ge = glob ? glob[e] : e;   // the energy's index in the outputs
   const bool okL = done[e] == 1 && res[e] <= accept;
   const bool okR = done[U + e] == 1 && res[U + e] <= accept;
-  if (status) status[e] = (okL && okR) ? NEGF_OK : NEGF_ERR_NOCONV;
+  if (status) status[ge] = (okL && okR) ? NEGF_OK : NEGF_ERR_NOCONV;
   if (iters_out) {
-    iters_out[2 * e] = iters[e];
-    iters_out[2 * e + 1] = iters[U + e];
+    iters_out[2 * ge] = iters[e];
+    iters_out[2 * ge + 1] = iters[U + e];
   }
   if (newton_out) {
-    newton_out[2 * e] = nsteps[e];
-    newton_out[2 * e + 1] = nsteps[U + e];
+    newton_out[2 * ge] = nsteps[e];
+    newton_out[2 * ge + 1] = nsteps[U + e];
   }
 }
 
@@ -1379,48 +1393,83 @@ __global__ void transmission_kernel(BMat Gam, BMat G, BMat K1, BMat K2, int n, d
   if (threadIdx.x == 0) T[u] = t;
 }
 
-// DOS(E) = -(1/pi) Im Tr[G S] over the BT pattern, one CTA per energy
-__global__ void dos_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* GRl, int e0, int eg, double* dos) {
-  const int u = blockIdx.x, e = e0 + u, eb = e - eg;   // eb: the energy's place in the G buffers
+// Traces of block products by 32 x 32 tiles (256 threads, warp w takes rows w, w+8, ..,
+// lane l columns c0 + l): acc[k] += sum_l X[r][l] Y[l][r] for row r = r0 + w + 8k of X,
+// with Y read as row segments into shared memory and used transposed, so that both
+// blocks are read with coalesced row segments.  ly(l, r) gives Y[l][r] (0 <= l, r < b).
+template <class LY>
+__device__ __forceinline__ void tile_rowdot(const zc* __restrict__ X, LY ly, int b, int r0, zc (*sm)[33], zc acc[4]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < b; c0 += 32) {
+    __syncthreads();   // the previous tile has been used
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int l = c0 + ty + 8 * k, r = r0 + tx;
+      sm[ty + 8 * k][tx] = (l < b && r < b) ? ly(l, r) : zmake(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = r0 + ty + 8 * k, l = c0 + tx;
+      if (r < b && l < b) zfma(acc[k], X[r * b + l], sm[tx][ty + 8 * k]);
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;   // valid in lane 0
+}
+
+// DOS(E) = -(1/pi) Im Tr[G S] over the BT pattern: part[u][i] = Im of block row i's share
+// (G_ii S_ii and, below the last block, G_{i,i+1} S_{i+1,i} + G_{i+1,i} S_{i,i+1}), one
+// CTA per (block, energy); dos_sum_kernel adds the shares in block order
+__global__ void __launch_bounds__(256) dos_part_kernel(DevView dv, const zc* GRd, const zc* GRu, const zc* GRl, int e0,
+                                                       int eg, double* part) {
+  const int i = blockIdx.x, u = blockIdx.y, eb = e0 + u - eg;   // eb: the energy's place in the G buffers
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
-  double acc = 0.0;   // accumulates Im Tr[G S]
-  for (int i = 0; i < nb; ++i) {
-    const zc* g = GRd + ((long long)eb * nb + i) * bb;
-    if (!dv.Sd) {
-      for (int r = threadIdx.x; r < b; r += blockDim.x) acc += g[(long long)r * b + r].y;
-    } else {
-      const zc* S = dv.Sd + i * bb;
-#pragma unroll 4
-      for (long long k = threadIdx.x; k < bb; k += blockDim.x) {   // sum_pq G_pq S_qp
-        const int p = (int)(k / b), q = (int)(k - (long long)p * b);
-        const zc v = zmul(g[k], S[(long long)q * b + p]);
-        acc += v.y;
-      }
-    }
-  }
-  if (dv.Su && GRu && GRl) {
-    for (int i = 0; i + 1 < nb; ++i) {
-      const zc* gu = GRu + ((long long)eb * (nb - 1) + i) * bb;
-      const zc* gl = GRl + ((long long)eb * (nb - 1) + i) * bb;
-      const zc* Su = dv.Su + i * bb;
-#pragma unroll 4
-      for (long long k = threadIdx.x; k < bb; k += blockDim.x) {
-        const int p = (int)(k / b), q = (int)(k - (long long)p * b);
-        // G_{i,i+1}[p][q] S_{i+1,i}[q][p] with S_{i+1,i} = S_up^H: S_{i+1,i}[q][p] = conj(Su[p][q])
-        acc += zmul(gu[k], zconj(Su[k])).y;
-        // G_{i+1,i}[p][q] S_{i,i+1}[q][p]
-        acc += zmul(gl[k], Su[(long long)q * b + p]).y;
-      }
-    }
-  }
+  __shared__ zc sm[32][33];
   __shared__ double red[32];
-  const double t = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) dos[e] = -t / M_PI;
+  const zc* g = GRd + ((long long)eb * nb + i) * bb;
+  double acc = 0.0;
+  if (!dv.Sd) {
+    for (int r = threadIdx.x; r < b; r += blockDim.x) acc += g[r * b + r].y;
+  } else {
+    const zc* S = dv.Sd + i * bb;
+    for (int r0 = 0; r0 < b; r0 += 32) {
+      zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
+      tile_rowdot(g, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
+      acc += t[0].y + t[1].y + t[2].y + t[3].y;
+    }
+  }
+  if (dv.Su && GRu && GRl && i + 1 < nb) {
+    const zc* gu = GRu + ((long long)eb * (nb - 1) + i) * bb;
+    const zc* gl = GRl + ((long long)eb * (nb - 1) + i) * bb;
+    const zc* Su = dv.Su + i * bb;
+    // G_{i,i+1}[p][q] S_{i+1,i}[q][p] with S_{i+1,i} = S_up^H: elementwise with conj(Su)
+    for (int k = threadIdx.x; k < b * b; k += blockDim.x) acc += zmul(gu[k], zconj(Su[k])).y;
+    // G_{i+1,i}[p][q] S_{i,i+1}[q][p]
+    for (int r0 = 0; r0 < b; r0 += 32) {
+      zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
+      tile_rowdot(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
+      acc += t[0].y + t[1].y + t[2].y + t[3].y;
+    }
+  }
+  const double v = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) part[(long long)u * nb + i] = v;
+}
+
+__global__ void dos_sum_kernel(const double* part, int nb, int e0, int U, double* dos) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= U) return;
+  double t = 0.0;
+  for (int i = 0; i < nb; ++i) t += part[(long long)u * nb + i];
+  dos[e0 + u] = -t / M_PI;
 }
 
 // J_i(E) = 2 Re Tr[(H_{i,i+1} - z S_{i,i+1}) G^<_{i+1,i}], one CTA per (energy, interface)
-__global__ void current_kernel(DevView dv, const zc* GLl, int e0, int eg, double* J) {
+__global__ void __launch_bounds__(256) current_kernel(DevView dv, const zc* GLl, int e0, int eg, double* J) {
   const int u = blockIdx.y, e = e0 + u, i = blockIdx.x;
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
@@ -1428,53 +1477,62 @@ __global__ void current_kernel(DevView dv, const zc* GLl, int e0, int eg, double
   const zc* g = GLl + ((long long)(e - eg) * (nb - 1) + i) * bb;
   const zc* H = dv.Hu + i * bb;
   const zc* S = dv.Su ? dv.Su + i * bb : nullptr;
-  double acc = 0.0;
-  // sum_pq A[p][q] G[q][p] with k running along G (coalesced reads of the per-energy block;
-  // A = H - z S is shared by all energies and read transposed from L2)
-#pragma unroll 4
-  for (long long k = threadIdx.x; k < bb; k += blockDim.x) {
-    const int q = (int)(k / b), p = (int)(k - (long long)q * b);
-    const long long t = (long long)p * b + q;
-    zc x = H[t];
-    if (S) x = zsub(x, zmul(z, S[t]));
-    acc += zmul(x, g[k]).x;
-  }
+  __shared__ zc sm[32][33];
   __shared__ double red[32];
-  const double t = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) J[(long long)e * (nb - 1) + i] = 2.0 * t;
+  // sum_qp G[q][p] A[p][q], A = H - z S (shared by all energies, read in row segments)
+  double acc = 0.0;
+  for (int r0 = 0; r0 < b; r0 += 32) {
+    zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
+    tile_rowdot(g, [&](int l, int r) {
+      zc x = H[l * b + r];
+      if (S) x = zsub(x, zmul(z, S[l * b + r]));
+      return x;
+    }, b, r0, sm, t);
+    acc += t[0].x + t[1].x + t[2].x + t[3].x;
+  }
+  const double v = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) J[(long long)e * (nb - 1) + i] = 2.0 * v;
 }
 
-// per-energy orbital occupation Re(-i (G^< S)_kk)/(2 pi) into nE[u][k], k over nb*b
-__global__ void density_energy_kernel(DevView dv, const zc* GLd, const zc* GLl, int e0, int eg, double* nE) {
-  const int u = blockIdx.y, e = e0 + u - eg;   // the energy's place in the G buffers
+// per-energy orbital occupation Re(-i (G^< S)_kk)/(2 pi) into nE[u][k], k = i b + r over
+// nb*b, one CTA per (block row i, energy)
+__global__ void __launch_bounds__(256) density_energy_kernel(DevView dv, const zc* GLd, const zc* GLl, int e0, int eg,
+                                                             double* nE) {
+  const int i = blockIdx.x, u = blockIdx.y, e = e0 + u - eg;   // the energy's place in the G buffers
   const int nb = dv.nb, b = dv.b;
   const long long bb = (long long)b * b;
   const long long N = (long long)nb * b;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(k / b), r = (int)(k - (long long)i * b);
-    const zc* gd = GLd + ((long long)e * nb + i) * bb;
-    zc m;
-    if (!dv.Sd) {
-      m = gd[(long long)r * b + r];
-    } else {
-      m = zmake(0.0, 0.0);
-      const zc* S = dv.Sd + i * bb;
-      for (int l = 0; l < b; ++l) zfma(m, gd[(long long)r * b + l], S[(long long)l * b + r]);
-      if (i + 1 < nb) {   // G^<_{i,i+1} S_{i+1,i},  G^<_{i,i+1}[r][l] = -conj(G^<_{i+1,i}[l][r]),  S_{i+1,i}[l][r] = conj(Su[r][l])
-        const zc* gl = GLl + ((long long)e * (nb - 1) + i) * bb;
-        const zc* Su = dv.Su + i * bb;
-        for (int l = 0; l < b; ++l) {
-          const zc a = zscale(zconj(gl[(long long)l * b + r]), -1.0);
-          zfma(m, a, zconj(Su[(long long)r * b + l]));
-        }
-      }
-      if (i > 0) {        // G^<_{i,i-1} S_{i-1,i}
-        const zc* gl = GLl + ((long long)e * (nb - 1) + (i - 1)) * bb;
-        const zc* Su = dv.Su + (i - 1) * bb;
-        for (int l = 0; l < b; ++l) zfma(m, gl[(long long)r * b + l], Su[(long long)l * b + r]);
-      }
+  const zc* gd = GLd + ((long long)e * nb + i) * bb;
+  double* out = nE + (long long)u * N + (long long)i * b;
+  if (!dv.Sd) {
+    for (int r = threadIdx.x; r < b; r += blockDim.x) out[r] = gd[r * b + r].y / (2.0 * M_PI);
+    return;
+  }
+  __shared__ zc sm[32][33];
+  const zc* S = dv.Sd + i * bb;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < b; r0 += 32) {
+    zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
+    // (G^<_ii S_ii)_rr
+    tile_rowdot(gd, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
+    if (i + 1 < nb) {
+      // (G^<_{i,i+1} S_{i+1,i})_rr with G^<_{i,i+1}[r][l] = -conj(G^<_{i+1,i}[l][r]) and
+      // S_{i+1,i}[l][r] = conj(Su[r][l]): -conj(sum_l Su[r][l] G^<_{i+1,i}[l][r]), whose
+      // imaginary part is that of the sum
+      const zc* gl = GLl + ((long long)e * (nb - 1) + i) * bb;
+      tile_rowdot(dv.Su + i * bb, [&](int l, int r) { return gl[l * b + r]; }, b, r0, sm, t);
     }
-    nE[(long long)u * N + k] = m.y / (2.0 * M_PI);   // Re(-i m) = Im m
+    if (i > 0) {   // (G^<_{i,i-1} S_{i-1,i})_rr
+      const zc* gl = GLl + ((long long)e * (nb - 1) + (i - 1)) * bb;
+      const zc* Su = dv.Su + (i - 1) * bb;
+      tile_rowdot(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double m = warp_sum(t[k].y);
+      const int r = r0 + ty + 8 * k;
+      if (tx == 0 && r < b) out[r] = m / (2.0 * M_PI);   // Re(-i m) = Im m
+    }
   }
 }
 
@@ -1526,7 +1584,10 @@ negf_status observables_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const Ob
     KCHECK();
   }
   if (ob.dos) {
-    dos_kernel<<<U, 256, 0, s>>>(dv, ob.GRd, ob.GRu, ob.GRl, e0, eg, ob.dos);
+    double* part = (double*)ws;   // [U][nb] block-row shares (ws holds >= N doubles per energy)
+    dos_part_kernel<<<dim3(nb, U), 256, 0, s>>>(dv, ob.GRd, ob.GRu, ob.GRl, e0, eg, part);
+    KCHECK();
+    dos_sum_kernel<<<(U + 255) / 256, 256, 0, s>>>(part, nb, e0, U, ob.dos);
     KCHECK();
   }
   if (ob.current && nb > 1) {
@@ -1535,8 +1596,7 @@ negf_status observables_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const Ob
   }
   if (ob.density) {
     double* nE = (double*)ws;
-    dim3 g1((unsigned)std::min<long long>((N + 255) / 256, 1024), U);
-    density_energy_kernel<<<g1, 256, 0, s>>>(dv, ob.GLd, ob.GLl, e0, eg, nE);
+    density_energy_kernel<<<dim3(nb, U), 256, 0, s>>>(dv, ob.GLd, ob.GLl, e0, eg, nE);
     KCHECK();
     density_accum_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 1024), 256, 0, s>>>(nE, ob.w, e0, U, N,
                                                                                                 ob.density);
@@ -2096,26 +2156,74 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
   const double target = 1e-13;   // Newton target
   const double accept = 1e-10;   // success threshold of the surface residual
   const bool any_warm = g0_L || g0_R;
-  for (int d = 0; d < sys->ndev; ++d) {
-    const int ne = sys->ne[d];
-    if (ne == 0) continue;
+  // the jobs: a device alone in its block size, or all devices of a block size as one
+  // batch of (device, energy) units (work list as in the sweeps)
+  std::vector<std::vector<int>> jobs;
+  {
+    std::vector<int> sizes;
+    for (int d = 0; d < sys->ndev; ++d)
+      if (sys->ne[d] > 0 && std::find(sizes.begin(), sizes.end(), sys->bs[d]) == sizes.end()) sizes.push_back(sys->bs[d]);
+    for (int bsz : sizes) {
+      std::vector<int> devs;
+      for (int d = 0; d < sys->ndev; ++d)
+        if (sys->ne[d] > 0 && sys->bs[d] == bsz) devs.push_back(d);
+      jobs.push_back(devs);
+    }
+  }
+  for (const std::vector<int>& devs : jobs) {
+    const bool batched = devs.size() > 1;
+    const int d = devs[0];
     const DevView dv = dev_view(sys, L, d);
     const long long* o = &L.off[8 * (size_t)d];
     const int b = dv.b;
     const long long bb = (long long)b * b;
     const size_t blk = sizeof(zc) * bb;
     const int nslots = 15;
+    std::vector<UnitDev> ud;
+    WorkList w;
+    std::vector<long long> off_s;   // per unit: its lead block's element offset (o[3] + e b^2)
+    int ne = sys->ne[d];
+    if (batched) {
+      for (int dd : devs) {
+        UnitDev x;
+        x.dv = dev_view(sys, L, dd);
+        ud.push_back(x);
+      }
+      w = make_worklist(sys, L, devs, bb);
+      ne = (int)w.unit_dev.size();
+      for (int k = 0; k < ne; ++k) off_s.push_back(L.off[8 * (size_t)devs[w.unit_dev[k]] + 3] + (long long)w.unit_e[k] * bb);
+    }
     // products on the sliced tensor-core path (FP64-class) when asked for and supported
     const int sl = (prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
     eng.mixed = sl;
-    const size_t per_unit = nslots * blk + 64 + zinv_scratch_bytes(b, 1, 0) + (sl ? ozt_scratch_bytes(b, 1) : 0);
-    int chunk = (int)std::min<size_t>((ctx->ws_bytes - 8192) / (2 * per_unit), (size_t)32767);
+    const size_t per_unit = nslots * blk + 64 + zinv_scratch_bytes(b, 1, 0) + (sl ? ozt_scratch_bytes(b, 1) : 0) +
+                            (batched ? 3 * sizeof(int) + sizeof(long long) : 0);
+    const size_t fixed = 8192 + (batched ? (sizeof(UnitDev) * ud.size() + 6 * 256) : 0);
+    if (ctx->ws_bytes <= fixed) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one OBC energy");
+    int chunk = (int)std::min<size_t>((ctx->ws_bytes - fixed) / (2 * per_unit), (size_t)32767);
     if (chunk < 1) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one OBC energy");
     chunk = std::min(chunk, ne);
     for (int e0 = 0; e0 < ne; e0 += chunk) {
       const int U = std::min(chunk, ne - e0);
       const int NU = 2 * U;
       char* p = (char*)ctx->ws;
+      // batched: the chunk's unit tables ahead of the slots
+      const UnitDev* t_udev = nullptr;
+      const int *t_dev = nullptr, *t_e = nullptr, *t_glob = nullptr;
+      const long long* t_off = nullptr;
+      if (batched) {
+        auto put = [&](const void* src, size_t bytes) -> const void* {
+          void* dst = p;
+          p += (bytes + 255) & ~(size_t)255;
+          return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess ? dst : nullptr;
+        };
+        t_udev = (const UnitDev*)put(ud.data(), sizeof(UnitDev) * ud.size());
+        t_dev = (const int*)put(w.unit_dev.data() + e0, sizeof(int) * U);
+        t_e = (const int*)put(w.unit_e.data() + e0, sizeof(int) * U);
+        t_glob = (const int*)put(w.unit_glob.data() + e0, sizeof(int) * U);
+        t_off = (const long long*)put(off_s.data() + e0, sizeof(long long) * U);
+        if (!t_udev || !t_dev || !t_e || !t_glob || !t_off) return fail(ctx, NEGF_ERR_CUDA, "copying the OBC unit tables failed");
+      }
       auto slot = [&]() { zc* q = (zc*)p; p += blk * (size_t)NU; return BMat{q, bb}; };
       BMat a00 = slot(), al0 = slot(), be0 = slot(), eps = slot(), epss = slot(), al = slot(), be = slot();
       BMat g = slot();
@@ -2140,6 +2248,9 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       eng.ozt_scratch = sl ? (void*)p : nullptr;
 
       LeadArgs la{dv, e0, U, a00.p, al0.p, be0.p, eps.p, epss.p, al.p, be.p};
+      la.udev = t_udev;
+      la.unit_dev = t_dev;
+      la.unit_e = t_e;
       dim3 eg((unsigned)std::min<long long>((bb + 255) / 256, 1024), NU);
       lead_init_kernel<<<eg, 256, 0, s>>>(la);
       KCHECK();
@@ -2197,9 +2308,10 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
 
       // ---- warm start: Newton from the guesses, kept only if converged and retarded
       if (any_warm) {
-        const zc* gl = g0_L ? (const zc*)g0_L + o[3] + (long long)e0 * bb : nullptr;
-        const zc* gr = g0_R ? (const zc*)g0_R + o[3] + (long long)e0 * bb : nullptr;
-        guess_init_kernel<<<eg, 256, 0, s>>>(g, gl, gr, U, b, warm);
+        const long long gb = batched ? 0 : o[3] + (long long)e0 * bb;   // batched: per-unit offsets
+        const zc* gl = g0_L ? (const zc*)g0_L + gb : nullptr;
+        const zc* gr = g0_R ? (const zc*)g0_R + gb : nullptr;
+        guess_init_kernel<<<eg, 256, 0, s>>>(g, gl, gr, U, b, warm, t_off);
         KCHECK();
         if ((st = residual(g, res, warm)) != NEGF_OK) return st;
         need_warm_kernel<<<(NU + 255) / 256, 256, 0, s>>>(warm, res, need, NU, target);
@@ -2267,21 +2379,23 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
           // units that took the step continue from T1/T2 (K, F of the accepted g)
         }
       }
-      if (gs_L)
-        CU(cudaMemcpyAsync((zc*)gs_L + o[3] + (long long)e0 * bb, g.p, blk * U, cudaMemcpyDeviceToDevice, s));
-      if (gs_R)
-        CU(cudaMemcpyAsync((zc*)gs_R + o[3] + (long long)e0 * bb, g.p + (long long)U * bb, blk * U,
-                           cudaMemcpyDeviceToDevice, s));
+      // the lead blocks of the chunk's energies in the outputs: contiguous for one device,
+      // at the work list's offsets for a batch
+      auto lead_out = [&](void* base) {
+        if (batched) return BMat{(zc*)base, 0, 0, 0, t_off};
+        return BMat{(zc*)base + o[3] + (long long)e0 * bb, bb};
+      };
+      if (gs_L) { ++ctx->launches; CU(bcopy(lead_out(gs_L), g, b, U, s)); }
+      if (gs_R) { ++ctx->launches; CU(bcopy(lead_out(gs_R), BMat{g.p + (long long)U * bb, bb}, b, U, s)); }
       // sigma = al0 g be0 (left units -> sigma_L, right -> sigma_R)
       CU(eng.gemm(T[0], al0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU));
-      zc* sL = (zc*)sigma_L + o[3] + (long long)e0 * bb;
-      zc* sR = (zc*)sigma_R + o[3] + (long long)e0 * bb;
-      CU(eng.gemm(BMat{sL, bb}, T[0], OP_N, be0, OP_N, ONE, NOMAT, ZERO, b, U));
-      CU(eng.gemm(BMat{sR, bb}, BMat{T[0].p + (long long)U * bb, bb}, OP_N,
+      CU(eng.gemm(lead_out(sigma_L), T[0], OP_N, be0, OP_N, ONE, NOMAT, ZERO, b, U));
+      CU(eng.gemm(lead_out(sigma_R), BMat{T[0].p + (long long)U * bb, bb}, OP_N,
                   BMat{be0.p + (long long)U * bb, bb}, OP_N, ONE, NOMAT, ZERO, b, U));
+      const long long ob = batched ? 0 : o[2] + e0;   // batched: per-unit energy indices
       obc_finish_kernel<<<(U + 127) / 128, 128, 0, s>>>(
-          done, res, it_arr, nsteps, U, status ? status + o[2] + e0 : nullptr,
-          iters ? iters + 2 * (o[2] + e0) : nullptr, newton ? newton + 2 * (o[2] + e0) : nullptr, accept);
+          done, res, it_arr, nsteps, U, status ? status + ob : nullptr, iters ? iters + 2 * ob : nullptr,
+          newton ? newton + 2 * ob : nullptr, accept, t_glob);
       KCHECK();
     }
   }
