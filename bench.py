@@ -48,6 +48,37 @@ def rank_energies(ne_per_rank, rank, world, e_min=-3.0, e_max=3.0):
     return grid[rank::world].copy()
 
 
+def rank_weights(ne_per_rank, rank, world, e_min=-3.0, e_max=3.0):
+    """Quadrature weights of one rank's energies: the trapezoid weights of the global
+    grid (ne_per_rank*world points) taken at this rank's points, so that the ranks'
+    weighted partial sums add up to the integral over the whole grid."""
+    grid = np.linspace(e_min, e_max, ne_per_rank * world)
+    return W.trapezoid_weights(grid)[rank::world].copy()
+
+
+def sum_over_ranks(t, world):
+    """In-place sum of a tensor over the ranks (the energy integral's exchange step)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
+def energy_integrals(density, current, w, ne, nb, world):
+    """The energy-integrated observables of the whole grid: the density (each rank's
+    output is already its weighted sum) and the interface currents
+    I_i = sum_E w(E) J_i(E), summed over the ranks.  Returns host numbers: the total
+    density, the mean interface current and the relative spread of the interface
+    currents (0 for a conserved current)."""
+    import torch
+    dens = sum_over_ranks(density.clone(), world)
+    cur = sum_over_ranks((w.view(ne, 1) * current.view(ne, nb - 1)).sum(0), world)
+    mean = float(cur.mean().item())
+    spread = float(((cur.max() - cur.min()) / max(abs(mean), 1e-300)).item())
+    return {"collective": f"all_reduce sum over {world} ranks" if world > 1 else "none (one rank)",
+            "density_total": float(dens.sum().item()), "current_mean": mean, "current_spread": spread}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -339,7 +370,7 @@ def run_gpu(args):
     out = P.allocate_outputs(sys_)
     fL = torch.from_numpy(dev.f_L()).cuda()
     fR = torch.from_numpy(dev.f_R()).cuda()
-    w = torch.from_numpy(dev.weights()).cuda()
+    w = torch.from_numpy(rank_weights(args.ne, rank, world)).cuda()
     stream = torch.cuda.current_stream()
 
     # the OBC products take the sliced FP64-class path with the mixed sweeps, FP64 otherwise
@@ -476,6 +507,10 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e / args.steps,
                "result": "T, DOS, current, density and status arrays"}
 
+    # ---- the energy integrals of the whole grid: every rank's weighted partial sums of
+    # the density and the interface currents, summed over the ranks (outside the timed region)
+    integrals = energy_integrals(out["density"], out["current"], w, ne, nb, world)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -505,6 +540,7 @@ def run_gpu(args):
         "rgf_only": {"value": rgf_value, "unit": UNIT, "ms_per_step": ms_rgf / args.steps},
         "fp64_comparison": cmp,
         "status": {"obc_not_converged": bad_obc, "rgf_flagged": bad},
+        "energy_integrals": integrals,
         "gpu_launches": prof["launches"],
         "kernel_time_share": shares,
         "roofline": roof,

@@ -20,10 +20,10 @@
 //    for NS = 8) are summed into one FP32 accumulator per d (NS accumulators in TMEM).
 //    With K = 2n real terms the largest group sum is NS * 64 * 64 * 2n < 2^24 for
 //    n <= 256: exact;
-//  * the epilogue forms sum_d G_d 2^(7(NS+1-d)) as two exact int64 halves, rebuilds
-//    each double with integer operations, scaled by 2^(e_A + e_B - 7 (NS + 1)), and
-//    adds them (GB300's FP64 pipe is narrow: the recombination stays in the integer
-//    units).
+//  * the epilogue forms sum_d G_d 2^(7(NS+1-d)) as two exact int64 halves, converts
+//    each exactly to a double, scales it by 2^(e_A + e_B - 7 (NS + 1)) with an integer
+//    addition to its exponent field, and adds the two (GB300's FP64 pipe is narrow:
+//    the recombination stays in the integer units but for that one addition).
 // The error is ~2^(1 - 7 NS) of |row of A| |column of B| (truncation of the digits and
 // of the pairs with s + t > NS + 1; 2^-55 for NS = 8): FP64-class for the RGF
 // tolerances.  (Rows and columns keep their own scales; entries far below their
@@ -287,17 +287,15 @@ __device__ __forceinline__ void halves(const uint32_t (&v)[NG][W], int j, long l
                   l);
 }
 
-// exact int64 (|v| < 2^53) times 2^p as an IEEE double, built with integer operations
+// exact int64 (|v| < 2^53) times 2^p as an IEEE double: the exact conversion, then p
+// added to the exponent field with one integer addition (0 when v = 0 or the result
+// would fall below the normal range, far below the tile's FP64-class accuracy)
 __device__ __forceinline__ double ldexp_int(long long v, int p) {
-  if (v == 0) return 0.0;
-  const unsigned long long neg = v < 0 ? 1ull : 0ull;
-  unsigned long long a = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  a <<= (lz - 11);                      // bit 52 set
-  const int ebits = 1023 + (63 - lz) + p;
-  if (ebits <= 0) return 0.0;           // underflow: far below FP64-class accuracy of the tile
-  const unsigned long long r = (neg << 63) | ((unsigned long long)ebits << 52) | (a & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)r);
+  const double x = __ll2double_rn(v);   // exact: |v| < 2^53
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7FF) + p;
+  if (v == 0 || e <= 0) return 0.0;
+  return __hiloint2double(hi + (int)((unsigned)p << 20), __double2loint(x));
 }
 
 // ---------------------------------------------------------------------------
@@ -859,8 +857,8 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
     // ---------------- epilogue: TMEM lanes 32*(warp % 4).., complex columns cbase..cbase+15.
     // The NG exact group sums (FP32 integers) are recombined in integers as two exact
     // int64 halves, sum_{d<HSPLIT} G_d 2^(7(HSPLIT-1-d)) and sum_{d>=HSPLIT} G_d 2^(7(NG-1-d)),
-    // each rebuilt into a double with integer operations and scaled by
-    // 2^(e_A + e_B - 7(NS+1)); the two doubles are added once.
+    // each converted exactly to a double and scaled by 2^(e_A + e_B - 7(NS+1)) through
+    // its exponent field; the two doubles are added once.
     if (nchunks > 0 && !mbar_wait(done, 0u)) s_fail = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int quad = warp & 3, cbase = (warp >> 2) * (TNC / 2);

@@ -189,7 +189,37 @@ struct AsmArgs {
   zc* SigG;                        // Sigma^>_ii slot (nullable)
   const zc *sigma_L, *sigma_R;     // lead self-energies of this device, [ne] blocks
   const double *fL, *fR;           // this device's occupations (nullable unless SigL)
+  // the energy-independent parts of this device's A blocks (asm_w_kernel), nullable:
+  // A_ii = E S_ii + Wd_i, A_{j,j+1} = E S_up_j + Wu_j, A_{j+1,j} = (E S_up_j + Wl_j)^H
+  // with E real: two FP64 FMAs per element instead of the complex z S - H
+  const zc *Wd = nullptr, *Wu = nullptr, *Wl = nullptr;
 };
+
+// Wd_i = -H_ii + i eta S_ii, Wu_j = -H_up_j + i eta S_up_j, Wl_j = -H_up_j - i eta S_up_j
+// (then z S - H = E S + W for z = E + i eta, and the conjugate transpose of E S_up + Wl
+// is z S_up^H - H_up^H)
+__global__ void asm_w_kernel(DevView dv, zc* Wd, zc* Wu, zc* Wl) {
+  const int i = blockIdx.y, b = dv.b, nb = dv.nb;
+  const int bb = b * b;
+  const double eta = dv.eta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < bb; k += gridDim.x * blockDim.x) {
+    const int r = k / b, c = k - r * b;
+    const zc sd = dv.Sd ? dv.Sd[(long long)i * bb + k] : zmake(r == c ? 1.0 : 0.0, 0.0);
+    const zc hd = dv.Hd[(long long)i * bb + k];
+    Wd[(long long)i * bb + k] = zmake(-hd.x - eta * sd.y, -hd.y + eta * sd.x);
+    if (i + 1 < nb) {
+      const zc su = dv.Su ? dv.Su[(long long)i * bb + k] : zmake(0.0, 0.0);
+      const zc hu = dv.Hu[(long long)i * bb + k];
+      Wu[(long long)i * bb + k] = zmake(-hu.x - eta * su.y, -hu.y + eta * su.x);
+      Wl[(long long)i * bb + k] = zmake(-hu.x + eta * su.y, -hu.y - eta * su.x);
+    }
+  }
+}
+
+// bytes of one device's W blocks (3 nb - 2 blocks, 1 KB aligned)
+size_t asm_w_bytes(int nb, int b) {
+  return ((sizeof(zc) * (size_t)b * b * (size_t)(3 * nb - 2)) + 1023) & ~(size_t)1023;
+}
 
 // One 32 x 32 tile of every requested block per CTA (32 x 8 threads, 4 rows each);
 // the conjugate-transposed terms (A_{j+1,j}, the lead Gamma's Sigma^H) are read as the
@@ -227,6 +257,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const double fo = (i == 0) ? (a.fL ? a.fL[e] : 0.0) : (a.fR ? a.fR[e] : 0.0);
   // transposed tiles: (row c0 + ty + 8k, column r0 + tx) of S_up, H_up (for A_{j+1,j}) and
   // of the lead Sigma (for Sigma^H), stored as [tx][ty + 8k]
+  const bool w = a.Wd != nullptr;   // E S + W form (E = Re z)
+  const double E = z.x;
   if (a.Alow) {
 #pragma unroll
     for (int k = 0; k < ASM_T / 8; ++k) {
@@ -234,7 +266,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
       zc sv = zmake(0.0, 0.0), hv = zmake(0.0, 0.0);
       if (rr < b && cc < b && offv) {
         if (a.dv.Su) sv = a.dv.Su[j * bb + (long long)rr * b + cc];
-        hv = a.dv.Hu[j * bb + (long long)rr * b + cc];
+        hv = w ? a.Wl[j * bb + (long long)rr * b + cc] : a.dv.Hu[j * bb + (long long)rr * b + cc];
       }
       tS[tx][ty + 8 * k] = sv;
       tH[tx][ty + 8 * k] = hv;
@@ -247,8 +279,19 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
     if (r >= b || c >= b) continue;
     const long long rc = (long long)r * b + c;
     if (a.Adiag) {
-      zc s = a.dv.Sd ? a.dv.Sd[i * bb + rc] : zmake(r == c ? 1.0 : 0.0, 0.0);
-      zc v = zsub(zmul(z, s), a.dv.Hd[i * bb + rc]);
+      zc v;
+      if (w) {
+        const zc wd = a.Wd[i * bb + rc];
+        if (a.dv.Sd) {
+          const zc sd = a.dv.Sd[i * bb + rc];
+          v = zmake(fma(E, sd.x, wd.x), fma(E, sd.y, wd.y));
+        } else {
+          v = zmake(r == c ? E + wd.x : wd.x, wd.y);
+        }
+      } else {
+        zc sd = a.dv.Sd ? a.dv.Sd[i * bb + rc] : zmake(r == c ? 1.0 : 0.0, 0.0);
+        v = zsub(zmul(z, sd), a.dv.Hd[i * bb + rc]);
+      }
       if (a.sc.sigR) v = zsub(v, a.sc.sigR[e * a.sc.e_stride + i * bb + rc]);
       if (i == 0) v = zsub(v, a.sigma_L[e * bb + rc]);
       if (i == nb - 1) v = zsub(v, a.sigma_R[e * bb + rc]);
@@ -256,12 +299,22 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
     }
     if (a.Aup) {   // A_{j,j+1} = z S_up - H_up
       zc v = zmake(0.0, 0.0);
-      if (offv) v = zsub(zmul(z, a.dv.Su ? a.dv.Su[j * bb + rc] : zmake(0.0, 0.0)), a.dv.Hu[j * bb + rc]);
+      if (offv) {
+        const zc su = a.dv.Su ? a.dv.Su[j * bb + rc] : zmake(0.0, 0.0);
+        if (w) {
+          const zc wu = a.Wu[j * bb + rc];
+          v = zmake(fma(E, su.x, wu.x), fma(E, su.y, wu.y));
+        } else {
+          v = zsub(zmul(z, su), a.dv.Hu[j * bb + rc]);
+        }
+      }
       a.Aup[u * bb + rc] = v;
     }
     if (a.Alow) {  // A_{j+1,j} = z S_up^H - H_up^H: element (r, c) = conj of (c, r)
-      const zc s = zconj(tS[ty + 8 * k][tx]);
-      a.Alow[u * bb + rc] = offv ? zsub(zmul(z, s), zconj(tH[ty + 8 * k][tx])) : zmake(0.0, 0.0);
+      const zc st = tS[ty + 8 * k][tx], ht = tH[ty + 8 * k][tx];
+      zc v = zmake(0.0, 0.0);
+      if (offv) v = w ? zmake(fma(E, st.x, ht.x), -fma(E, st.y, ht.y)) : zsub(zmul(z, zconj(st)), zconj(ht));
+      a.Alow[u * bb + rc] = v;
     }
   }
   if (!a.SigL && !a.SigG) return;
@@ -498,6 +551,7 @@ struct RgfIO {
   int32_t* status;               // device-offset, nullable
   bool lesser;
   bool greater = false;          // also G^> (with `lesser`)
+  const zc* W = nullptr;         // this device's W blocks (asm_w_kernel; Wd, Wu, Wl in turn), nullable
 };
 
 // The (device, energy) units of the devices of an uneven batch that share one block size,
@@ -576,6 +630,11 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   a.dv = dv; a.sc = sc; a.e0 = e0; a.units = U;
   a.sigma_L = io.sigma_L; a.sigma_R = io.sigma_R; a.fL = io.fL; a.fR = io.fR;
   if (bp) { a.udev = bp->udev; a.unit_dev = bp->unit_dev; a.unit_e = bp->unit_e; }
+  if (io.W && !bp) {
+    a.Wd = io.W;
+    a.Wu = io.W + (long long)nb * bb;
+    a.Wl = a.Wu + (long long)(nb - 1) * bb;
+  }
   int32_t* st = bp ? bp->st_units : (io.status ? io.status + e0 : nullptr);
   const int* act = nullptr;   // this step's mask (uneven batch), else every unit
 
@@ -1131,6 +1190,29 @@ __global__ void residual_kernel(BMat F, int n, double* res, const int* active) {
   }
 }
 
+// redo[u] = 1 for an active unit whose refined inverse is not FP64-class: the residual
+// R = I - M X left by the last refinement step (the step from X to X + X R leaves an
+// error of the order of |R|^2) has a Frobenius norm above tol, or is not finite
+__global__ void refine_check_kernel(BMat R, int n, const int* active, double tol, int* redo) {
+  const int u = blockIdx.x;
+  if (active && !active[u]) {
+    if (threadIdx.x == 0) redo[u] = 0;
+    return;
+  }
+  const zc* r = R.at(u);
+  const int nn = n * n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) s += r[i].x * r[i].x + r[i].y * r[i].y;
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    redo[u] = (s <= tol * tol) ? 0 : 1;   // NaN: redo
+  }
+}
+
 // Smith step bookkeeping: S += inc; conv if max|inc| <= tol max|S|; rebalance P, Q
 __global__ void smith_accum_kernel(BMat S, BMat inc, int n, int* act, double tol) {
   const int u = blockIdx.x;
@@ -1394,11 +1476,13 @@ __global__ void transmission_kernel(BMat Gam, BMat G, BMat K1, BMat K2, int n, d
 }
 
 // Traces of block products by 32 x 32 tiles (256 threads, warp w takes rows w, w+8, ..,
-// lane l columns c0 + l): acc[k] += sum_l X[r][l] Y[l][r] for row r = r0 + w + 8k of X,
-// with Y read as row segments into shared memory and used transposed, so that both
-// blocks are read with coalesced row segments.  ly(l, r) gives Y[l][r] (0 <= l, r < b).
-template <class LY>
-__device__ __forceinline__ void tile_rowdot(const zc* __restrict__ X, LY ly, int b, int r0, zc (*sm)[33], zc acc[4]) {
+// lane l columns c0 + l): acc[k] += Re (PART 0) or Im (PART 1) of sum_l X[r][l] Y[l][r]
+// for row r = r0 + w + 8k of X, with Y read as row segments into shared memory and used
+// transposed, so that both blocks are read with coalesced row segments (one part: two
+// FP64 FMAs per element).  ly(l, r) gives Y[l][r] (0 <= l, r < b).
+template <int PART, class LY>
+__device__ __forceinline__ void tile_rowdot(const zc* __restrict__ X, LY ly, int b, int r0, zc (*sm)[33],
+                                            double acc[4]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int c0 = 0; c0 < b; c0 += 32) {
     __syncthreads();   // the previous tile has been used
@@ -1411,7 +1495,10 @@ __device__ __forceinline__ void tile_rowdot(const zc* __restrict__ X, LY ly, int
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int r = r0 + ty + 8 * k, l = c0 + tx;
-      if (r < b && l < b) zfma(acc[k], X[r * b + l], sm[tx][ty + 8 * k]);
+      if (r < b && l < b) {
+        const zc x = X[r * b + l], y = sm[tx][ty + 8 * k];
+        acc[k] = PART == 0 ? fma(x.x, y.x, fma(-x.y, y.y, acc[k])) : fma(x.x, y.y, fma(x.y, y.x, acc[k]));
+      }
     }
   }
 }
@@ -1438,9 +1525,9 @@ __global__ void __launch_bounds__(256) dos_part_kernel(DevView dv, const zc* GRd
   } else {
     const zc* S = dv.Sd + i * bb;
     for (int r0 = 0; r0 < b; r0 += 32) {
-      zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
-      tile_rowdot(g, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
-      acc += t[0].y + t[1].y + t[2].y + t[3].y;
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      tile_rowdot<1>(g, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
+      acc += t[0] + t[1] + t[2] + t[3];
     }
   }
   if (dv.Su && GRu && GRl && i + 1 < nb) {
@@ -1448,12 +1535,12 @@ __global__ void __launch_bounds__(256) dos_part_kernel(DevView dv, const zc* GRd
     const zc* gl = GRl + ((long long)eb * (nb - 1) + i) * bb;
     const zc* Su = dv.Su + i * bb;
     // G_{i,i+1}[p][q] S_{i+1,i}[q][p] with S_{i+1,i} = S_up^H: elementwise with conj(Su)
-    for (int k = threadIdx.x; k < b * b; k += blockDim.x) acc += zmul(gu[k], zconj(Su[k])).y;
+    for (int k = threadIdx.x; k < b * b; k += blockDim.x) acc = fma(gu[k].y, Su[k].x, fma(-gu[k].x, Su[k].y, acc));
     // G_{i+1,i}[p][q] S_{i,i+1}[q][p]
     for (int r0 = 0; r0 < b; r0 += 32) {
-      zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
-      tile_rowdot(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
-      acc += t[0].y + t[1].y + t[2].y + t[3].y;
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      tile_rowdot<1>(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
+      acc += t[0] + t[1] + t[2] + t[3];
     }
   }
   const double v = block_sum<256>(acc, red);
@@ -1482,13 +1569,13 @@ __global__ void __launch_bounds__(256) current_kernel(DevView dv, const zc* GLl,
   // sum_qp G[q][p] A[p][q], A = H - z S (shared by all energies, read in row segments)
   double acc = 0.0;
   for (int r0 = 0; r0 < b; r0 += 32) {
-    zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
-    tile_rowdot(g, [&](int l, int r) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    tile_rowdot<0>(g, [&](int l, int r) {
       zc x = H[l * b + r];
       if (S) x = zsub(x, zmul(z, S[l * b + r]));
       return x;
     }, b, r0, sm, t);
-    acc += t[0].x + t[1].x + t[2].x + t[3].x;
+    acc += t[0] + t[1] + t[2] + t[3];
   }
   const double v = block_sum<256>(acc, red);
   if (threadIdx.x == 0) J[(long long)e * (nb - 1) + i] = 2.0 * v;
@@ -1512,24 +1599,24 @@ __global__ void __launch_bounds__(256) density_energy_kernel(DevView dv, const z
   const zc* S = dv.Sd + i * bb;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int r0 = 0; r0 < b; r0 += 32) {
-    zc t[4] = {zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0), zmake(0.0, 0.0)};
+    double t[4] = {0.0, 0.0, 0.0, 0.0};   // imaginary parts
     // (G^<_ii S_ii)_rr
-    tile_rowdot(gd, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
+    tile_rowdot<1>(gd, [&](int l, int r) { return S[l * b + r]; }, b, r0, sm, t);
     if (i + 1 < nb) {
       // (G^<_{i,i+1} S_{i+1,i})_rr with G^<_{i,i+1}[r][l] = -conj(G^<_{i+1,i}[l][r]) and
       // S_{i+1,i}[l][r] = conj(Su[r][l]): -conj(sum_l Su[r][l] G^<_{i+1,i}[l][r]), whose
       // imaginary part is that of the sum
       const zc* gl = GLl + ((long long)e * (nb - 1) + i) * bb;
-      tile_rowdot(dv.Su + i * bb, [&](int l, int r) { return gl[l * b + r]; }, b, r0, sm, t);
+      tile_rowdot<1>(dv.Su + i * bb, [&](int l, int r) { return gl[l * b + r]; }, b, r0, sm, t);
     }
     if (i > 0) {   // (G^<_{i,i-1} S_{i-1,i})_rr
       const zc* gl = GLl + ((long long)e * (nb - 1) + (i - 1)) * bb;
       const zc* Su = dv.Su + (i - 1) * bb;
-      tile_rowdot(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
+      tile_rowdot<1>(gl, [&](int l, int r) { return Su[l * b + r]; }, b, r0, sm, t);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double m = warp_sum(t[k].y);
+      const double m = warp_sum(t[k]);
       const int r = r0 + ty + 8 * k;
       if (tx == 0 && r < b) out[r] = m / (2.0 * M_PI);   // Re(-i m) = Im m
     }
@@ -1865,15 +1952,29 @@ static negf_status rgf_common(Ctx* ctx, const negf_system* sys, negf_precision p
     io.status = status ? status + o[2] : nullptr;
     io.lesser = lesser;
     const size_t per = rgf_bytes_per_energy(dv.nb, dv.b, io, eng.mixed);
-    int chunk = (int)std::min<size_t>(ctx->ws_bytes / per, (size_t)65535);
+    // the device's W blocks (energy-independent part of A) ahead of the chunk workspace,
+    // when there is room for them next to one energy
+    const size_t wb = asm_w_bytes(dv.nb, dv.b);
+    const bool use_w = ctx->ws_bytes >= wb + per;
+    char* ws = (char*)ctx->ws + (use_w ? wb : 0);
+    int chunk = (int)std::min<size_t>((ctx->ws_bytes - (use_w ? wb : 0)) / per, (size_t)65535);
     if (chunk < 1)
       return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one energy of this device needs " +
                                            std::to_string(per) + " bytes");
     chunk = std::min(chunk, ne);
+    if (use_w) {
+      zc* W = (zc*)ctx->ws;
+      const long long bb = (long long)dv.b * dv.b;
+      ++ctx->launches;
+      asm_w_kernel<<<dim3((unsigned)std::min<long long>((bb + 255) / 256, 1024), dv.nb), 256, 0, s>>>(
+          dv, W, W + dv.nb * bb, W + (2LL * dv.nb - 1) * bb);
+      CU(cudaGetLastError());
+      io.W = W;
+    }
     for (int e0 = 0; e0 < ne; e0 += chunk) {
       const int U = std::min(chunk, ne - e0);
       eng.inv_scratch = nullptr;
-      st = rgf_chunk(ctx, eng, dv, sc, io, e0, U, (char*)ctx->ws);
+      st = rgf_chunk(ctx, eng, dv, sc, io, e0, U, ws);
       if (st != NEGF_OK) return st;
     }
   }
@@ -2240,6 +2341,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       int* keep = (int*)p; p += sizeof(int) * NU;     // warm result kept
       int* cold = (int*)p; p += sizeof(int) * NU;     // unit goes through the decimation
       int* nsteps = (int*)p; p += sizeof(int) * NU;   // Newton steps taken
+      int* redo = (int*)p; p += sizeof(int) * NU;     // refined inverse redone in FP64
       int* n_active = (int*)p; p += 16;
       p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
       eng.inv_scratch = zinv_scratch_bytes(b, NU, 0) ? (void*)p : nullptr;
@@ -2257,6 +2359,22 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       CU(cudaMemsetAsync(nsteps, 0, sizeof(int) * NU, s));
       CU(cudaMemsetAsync(keep, 0, sizeof(int) * NU, s));
 
+      // X = M^{-1} for the units in `mask` (all when NULL), FP64-class.  Mixed: FP32
+      // Gauss-Jordan with two refinement steps on the sliced products (residuals in
+      // T0, T1), then FP64 Gauss-Jordan for the units whose last residual shows that
+      // the refinement did not reach FP64 class (ill-conditioned eps near band edges);
+      // FP64 precision: FP64 Gauss-Jordan
+      auto lead_inverse = [&](BMat X, BMat M, const int* mask) -> negf_status {
+        if (!sl) {
+          CU(eng.inv(X, M, b, NU, mask, 0, nullptr));
+          return NEGF_OK;
+        }
+        CU(eng.inverse(X, M, b, NU, nullptr, T[0], T[1], 2, mask));
+        refine_check_kernel<<<NU, 256, 0, s>>>(T[0], b, mask, 1e-7, redo);
+        KCHECK();
+        CU(eng.inv(X, M, b, NU, redo, 0, nullptr));
+        return NEGF_OK;
+      };
       auto residual = [&](BMat X, double* out, const int* mask) -> negf_status {
         CU(eng.gemm(T[0], al0, OP_N, X, OP_N, ONE, NOMAT, ZERO, b, NU, mask));               // al X
         CU(eng.gemm(T[1], T[0], OP_N, be0, OP_N, MONE, a00, ONE, b, NU, mask));              // K = a00 - al X be
@@ -2350,7 +2468,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
             if (ctx->h_pinned[0] == 0) break;
           }
           if (it == max_iter) break;
-          CU(eng.inv(g, eps, b, NU, act, 0, nullptr));                     // g = eps^{-1}
+          if ((st = lead_inverse(g, eps, act)) != NEGF_OK) return st;        // g = eps^{-1}
           CU(eng.gemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // al g
           CU(eng.gemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // be g
           CU(eng.gemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // al g be
@@ -2363,7 +2481,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
           std::swap(be, T[5]);
         }
         // ---- surface function and its residual
-        CU(eng.inv(g, epss, b, NU, any_warm ? cold : nullptr, 0, nullptr));
+        if ((st = lead_inverse(g, epss, any_warm ? cold : nullptr)) != NEGF_OK) return st;
         if ((st = residual(g, res, any_warm ? cold : nullptr)) != NEGF_OK) return st;
         // ---- Newton polishing of the decimation result above the target
         set_need_kernel<<<(NU + 255) / 256, 256, 0, s>>>(res, need, NU, target, cold);
@@ -2502,13 +2620,25 @@ negf_status negf_rgf_observables(negf_ctx* c, const negf_system* sys, negf_preci
     io.GRd = io.GRu = io.GRl = io.GLd = io.GLl = (zc*)ctx->ws;
     const int sl = (T && prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
     const size_t per = gblocks * blk + rgf_bytes_per_energy(nb, b, io, eng.mixed) + observables_bytes_per_energy(dv, sl) + 3072;
-    int chunk = (int)std::min<size_t>(ctx->ws_bytes / per, (size_t)65535);
+    // the device's W blocks ahead of the chunks, when there is room for them next to one energy
+    const size_t wb = asm_w_bytes(nb, b);
+    const bool use_w = ctx->ws_bytes >= wb + per;
+    int chunk = (int)std::min<size_t>((ctx->ws_bytes - (use_w ? wb : 0)) / per, (size_t)65535);
     if (chunk < 1)
       return fail(ctx, NEGF_ERR_NOMEM, "workspace too small: one energy of this device needs " + std::to_string(per) + " bytes");
     chunk = std::min(chunk, ne);
+    io.W = nullptr;
+    if (use_w) {
+      zc* W = (zc*)ctx->ws;
+      ++ctx->launches;
+      asm_w_kernel<<<dim3((unsigned)std::min<long long>((bb + 255) / 256, 1024), nb), 256, 0, s>>>(
+          dv, W, W + nb * bb, W + (2LL * nb - 1) * bb);
+      CU(cudaGetLastError());
+      io.W = W;
+    }
     for (int e0 = 0; e0 < ne; e0 += chunk) {
       const int U = std::min(chunk, ne - e0);
-      char* p = (char*)ctx->ws;
+      char* p = (char*)ctx->ws + (use_w ? wb : 0);
       auto take = [&](size_t nblocks) { zc* q = (zc*)p; p += blk * nblocks * (size_t)U; return q; };
       io.GRd = take(nb);
       io.GLd = take(nb);

@@ -120,3 +120,51 @@ def test_traffic_record_matches_the_kernel_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("gemm_oz") is None
     assert bench.traffic_for("inv_f32") is None
+
+
+def _integral_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ne, nb, norb = 16, 5, 3
+    E = bench.rank_energies(ne, rank, world)
+    w = torch.from_numpy(bench.rank_weights(ne, rank, world))
+    # a rank's outputs as negf_observables leaves them: its weighted density sum and the
+    # per-energy interface currents (conserved: the same for every interface)
+    nE = np.stack([np.cos(E * (k + 1)) for k in range(norb)], axis=1)            # [ne][orbitals]
+    density = torch.from_numpy((w.numpy()[:, None] * nE).sum(0))
+    current = torch.from_numpy(np.repeat(np.exp(-E * E)[:, None], nb - 1, axis=1).reshape(-1).copy())
+    out = bench.energy_integrals(density, current, w, ne, nb, world)
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_energy_integrals_sum_over_two_gloo_ranks():
+    """The ranks' weighted partial sums add up to the trapezoid integral over the whole
+    grid (the exchange step of energy-sharded runs)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_integral_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in ps), key=lambda x: x[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    grid = np.linspace(-3.0, 3.0, 32)
+    dens_ref = sum(np.trapezoid(np.cos(grid * (k + 1)), grid) for k in range(3))
+    cur_ref = np.trapezoid(np.exp(-grid * grid), grid)
+    for _, out in res:
+        assert out["collective"] == "all_reduce sum over 2 ranks"
+        assert abs(out["density_total"] - dens_ref) < 1e-12
+        assert abs(out["current_mean"] - cur_ref) < 1e-12
+        assert out["current_spread"] < 1e-12
+
+
+def test_rank_weights_one_rank_is_the_local_trapezoid():
+    assert np.array_equal(bench.rank_weights(64, 0, 1), bench.W.trapezoid_weights(np.linspace(-3.0, 3.0, 64)))
+    parts = [bench.rank_weights(8, r, 4) for r in range(4)]
+    assert abs(sum(p.sum() for p in parts) - 6.0) < 1e-12
