@@ -64,19 +64,19 @@ def sum_over_ranks(t, world):
     return t
 
 
-def energy_integrals(density, current, w, ne, nb, world):
-    """The energy-integrated observables of the whole grid: the density (each rank's
-    output is already its weighted sum) and the interface currents
-    I_i = sum_E w(E) J_i(E), summed over the ranks.  Returns host numbers: the total
-    density, the mean interface current and the relative spread of the interface
-    currents (0 for a conserved current)."""
-    import torch
-    dens = sum_over_ranks(density.clone(), world)
+def energy_integrals(density, current, T, fL, fR, w, ne, nb, world):
+    """The energy-integrated observables of the whole grid, summed over the ranks (each
+    rank's density output is already its weighted sum): the total density, the
+    interface currents I_i = sum_E w(E) J_i(E) at the first and the last interface, and
+    the Landauer current sum_E w(E) T(E) (f_L - f_R).  In a ballistic device the
+    interface currents differ from one another only by the eta sink of the blocks
+    between them (Sec. III's conservation check holds up to O(eta))."""
     cur = sum_over_ranks((w.view(ne, 1) * current.view(ne, nb - 1)).sum(0), world)
-    mean = float(cur.mean().item())
-    spread = float(((cur.max() - cur.min()) / max(abs(mean), 1e-300)).item())
+    dens = sum_over_ranks(density.sum().reshape(1).clone(), world)
+    land = sum_over_ranks((w * T * (fL - fR)).sum().reshape(1), world)
     return {"collective": f"all_reduce sum over {world} ranks" if world > 1 else "none (one rank)",
-            "density_total": float(dens.sum().item()), "current_mean": mean, "current_spread": spread}
+            "density_total": float(dens.item()), "current_interface_first": float(cur[0].item()),
+            "current_interface_last": float(cur[-1].item()), "current_landauer": float(land.item())}
 
 
 def dist_env():
@@ -509,7 +509,7 @@ def run_gpu(args):
 
     # ---- the energy integrals of the whole grid: every rank's weighted partial sums of
     # the density and the interface currents, summed over the ranks (outside the timed region)
-    integrals = energy_integrals(out["density"], out["current"], w, ne, nb, world)
+    integrals = energy_integrals(out["density"], out["current"], out["T"], fL, fR, w, ne, nb, world)
 
     if rank != 0:
         if world > 1:

@@ -226,6 +226,9 @@ size_t asm_w_bytes(int nb, int b) {
 // transposed tile through shared memory, so that every global access is a row segment.
 constexpr int ASM_T = 32;
 
+// USE_W: the E S + W form (a.Wd, a.Wu, a.Wl set); a compile-time switch, so that the
+// compiler does not merge the two forms' arithmetic into one predicated sequence
+template <bool USE_W>
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const int u = blockIdx.y;
   int e;
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   const double fo = (i == 0) ? (a.fL ? a.fL[e] : 0.0) : (a.fR ? a.fR[e] : 0.0);
   // transposed tiles: (row c0 + ty + 8k, column r0 + tx) of S_up, H_up (for A_{j+1,j}) and
   // of the lead Sigma (for Sigma^H), stored as [tx][ty + 8k]
-  const bool w = a.Wd != nullptr;   // E S + W form (E = Re z)
+  constexpr bool w = USE_W;   // E S + W form (E = Re z)
   const double E = z.x;
   if (a.Alow) {
 #pragma unroll
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
     if (a.Alow) {  // A_{j+1,j} = z S_up^H - H_up^H: element (r, c) = conj of (c, r)
       const zc st = tS[ty + 8 * k][tx], ht = tH[ty + 8 * k][tx];
       zc v = zmake(0.0, 0.0);
-      if (offv) v = w ? zmake(fma(E, st.x, ht.x), -fma(E, st.y, ht.y)) : zsub(zmul(z, zconj(st)), zconj(ht));
+      if (offv) v = w ? zmake(fma(E, st.x, ht.x), fma(-E, st.y, -ht.y)) : zsub(zmul(z, zconj(st)), zconj(ht));
       a.Alow[u * bb + rc] = v;
     }
   }
@@ -367,7 +370,10 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
 cudaError_t assemble(const AsmArgs& a, cudaStream_t s) {
   if (a.units <= 0) return cudaSuccess;
   const int nt = (a.dv.b + ASM_T - 1) / ASM_T;
-  assemble_kernel<<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
+  if (a.Wd)
+    assemble_kernel<true><<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
+  else
+    assemble_kernel<false><<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -495,6 +501,12 @@ struct Engine {
     if (refine < 0) refine = (mixed == 1) ? 2 : 1;
     cudaError_t e = inv(X, M, n, units, active, mixed ? 1 : 0, status);
     if (e != cudaSuccess || !mixed) return e;
+    return refine_steps(X, M, n, units, T1, T2, refine, active);
+  }
+  // `refine` steps X <- X + X (I - M X) (mixed modes); T1 keeps the last residual
+  // I - M X (of the X before the last step)
+  cudaError_t refine_steps(BMat X, BMat M, int n, int units, BMat T1, BMat T2, int refine, const int* active) {
+    cudaError_t e = cudaSuccess;
     const long long nn = (long long)n * n;
     dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), units);
     for (int k = 0; k < refine; ++k) {
@@ -1126,10 +1138,12 @@ __global__ void lead_norm_kernel(BMat al, BMat be, int n, int mode, double* ref,
   const long long nn = (long long)n * n;
   const zc* x = al.at(u);
   const zc* y = be.at(u);
+  // the largest |entry|, from the squared moduli (two FP64 operations per entry; one
+  // square root per block)
   double m = 0.0;
   for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
-    m = fmax(m, hypot(x[i].x, x[i].y));
-    m = fmax(m, hypot(y[i].x, y[i].y));
+    m = fmax(m, zabs2(x[i]));
+    m = fmax(m, zabs2(y[i]));
   }
   __shared__ double red[32];
   for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
@@ -1137,6 +1151,7 @@ __global__ void lead_norm_kernel(BMat al, BMat be, int n, int mode, double* ref,
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    m = sqrt(m);
     if (mode == 0) {
       ref[u] = fmax(m, 1e-300);
       done[u] = 0;
@@ -1220,12 +1235,12 @@ __global__ void smith_accum_kernel(BMat S, BMat inc, int n, int* act, double tol
   const long long nn = (long long)n * n;
   zc* s = S.at(u);
   const zc* d = inc.at(u);
-  double mi = 0.0, ms = 0.0;
+  double mi = 0.0, ms = 0.0;   // squared moduli
   for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
     zc v = zadd(s[i], d[i]);
     s[i] = v;
-    mi = fmax(mi, hypot(d[i].x, d[i].y));
-    ms = fmax(ms, hypot(v.x, v.y));
+    mi = fmax(mi, zabs2(d[i]));
+    ms = fmax(ms, zabs2(v));
   }
   __shared__ double r1[32], r2[32];
   for (int off = 16; off > 0; off >>= 1) {
@@ -1236,6 +1251,8 @@ __global__ void smith_accum_kernel(BMat S, BMat inc, int n, int* act, double tol
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { mi = fmax(mi, r1[w]); ms = fmax(ms, r2[w]); }
+    mi = sqrt(mi);
+    ms = sqrt(ms);
     if (mi <= tol * fmax(ms, 1e-300) || !isfinite(ms)) act[u] = 0;
   }
 }
@@ -1246,10 +1263,10 @@ __global__ void balance_kernel(BMat P, BMat Q, int n, const int* act) {
   const long long nn = (long long)n * n;
   zc* p = P.at(u);
   zc* q = Q.at(u);
-  double mp = 0.0, mq = 0.0;
+  double mp = 0.0, mq = 0.0;   // squared moduli
   for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
-    mp = fmax(mp, hypot(p[i].x, p[i].y));
-    mq = fmax(mq, hypot(q[i].x, q[i].y));
+    mp = fmax(mp, zabs2(p[i]));
+    mq = fmax(mq, zabs2(q[i]));
   }
   __shared__ double r1[32], r2[32];
   __shared__ double sc;
@@ -1261,7 +1278,7 @@ __global__ void balance_kernel(BMat P, BMat Q, int n, const int* act) {
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { mp = fmax(mp, r1[w]); mq = fmax(mq, r2[w]); }
-    sc = (mp > 0.0 && mq > 0.0) ? sqrt(mq / mp) : 1.0;
+    sc = (mp > 0.0 && mq > 0.0) ? sqrt(sqrt(mq) / sqrt(mp)) : 1.0;
   }
   __syncthreads();
   const double s = sc;
@@ -2144,7 +2161,7 @@ negf_status negf_scba(negf_ctx* c, const negf_system* sys, negf_precision prec, 
     CU(cudaStreamSynchronize(s));
     double h[3];
     memcpy(h, ctx->h_pinned, sizeof(h));
-    last = std::max(h[0], h[1]) / std::max(h[2], 1e-300);
+    last = std::sqrt(std::max(h[0], h[1])) / std::max(std::sqrt(h[2]), 1e-300);   // the stats are squared
     if (last < tol) break;
   }
   if (iters) *iters = it;
@@ -2371,6 +2388,11 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
         }
         CU(eng.inverse(X, M, b, NU, nullptr, T[0], T[1], 2, mask));
         refine_check_kernel<<<NU, 256, 0, s>>>(T[0], b, mask, 1e-7, redo);
+        KCHECK();
+        // units whose refinement converges slowly (kappa(eps) up to ~1e7) take two more
+        // steps; FP64 Gauss-Jordan for what is left
+        CU(eng.refine_steps(X, M, b, NU, T[0], T[1], 2, redo));
+        refine_check_kernel<<<NU, 256, 0, s>>>(T[0], b, redo, 1e-7, redo);
         KCHECK();
         CU(eng.inv(X, M, b, NU, redo, 0, nullptr));
         return NEGF_OK;

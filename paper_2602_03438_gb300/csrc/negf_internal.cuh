@@ -37,6 +37,8 @@ __host__ __device__ __forceinline__ zc zmul(zc a, zc b) {
 }
 __host__ __device__ __forceinline__ zc zconj(zc a) { return make_double2(a.x, -a.y); }
 __host__ __device__ __forceinline__ zc zscale(zc a, double s) { return make_double2(a.x * s, a.y * s); }
+// |a|^2 (two FP64 operations, where hypot takes many on GB300's narrow FP64 pipe)
+__host__ __device__ __forceinline__ double zabs2(zc a) { return fma(a.x, a.x, a.y * a.y); }
 // a += b * c
 __host__ __device__ __forceinline__ void zfma(zc& a, zc b, zc c) {
   a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));

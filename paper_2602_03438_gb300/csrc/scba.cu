@@ -107,16 +107,17 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// stats[0] = max |SLn - SL|, [1] = max |SGn - SG|, [2] = max(|SLn|, |SGn|); then
-// SL += mix (SLn - SL), SG += mix (SGn - SG), SR = (SG - SL) / 2
+// stats[0] = max |SLn - SL|^2, [1] = max |SGn - SG|^2, [2] = max(|SLn|, |SGn|)^2 (squared
+// moduli: two FP64 operations per entry); then SL += mix (SLn - SL), SG += mix (SGn - SG),
+// SR = (SG - SL) / 2
 __global__ void scba_mix_kernel(zc* SL, zc* SG, zc* SR, const zc* SLn, const zc* SGn, long long n, double mix,
                                 double* stats) {
   double dl = 0.0, dg = 0.0, sc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const zc l = SL[i], g = SG[i], ln = SLn[i], gn = SGn[i];
-    dl = fmax(dl, hypot(ln.x - l.x, ln.y - l.y));
-    dg = fmax(dg, hypot(gn.x - g.x, gn.y - g.y));
-    sc = fmax(sc, fmax(hypot(ln.x, ln.y), hypot(gn.x, gn.y)));
+    dl = fmax(dl, zabs2(zsub(ln, l)));
+    dg = fmax(dg, zabs2(zsub(gn, g)));
+    sc = fmax(sc, fmax(zabs2(ln), zabs2(gn)));
     const zc l2 = zadd(l, zscale(zsub(ln, l), mix)), g2 = zadd(g, zscale(zsub(gn, g), mix));
     SL[i] = l2;
     SG[i] = g2;

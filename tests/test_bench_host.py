@@ -131,12 +131,16 @@ def _integral_worker(rank, world, port, q):
     ne, nb, norb = 16, 5, 3
     E = bench.rank_energies(ne, rank, world)
     w = torch.from_numpy(bench.rank_weights(ne, rank, world))
-    # a rank's outputs as negf_observables leaves them: its weighted density sum and the
-    # per-energy interface currents (conserved: the same for every interface)
+    # a rank's outputs as negf_observables leaves them: its weighted density sum, the
+    # per-energy interface currents (conserved: T (f_L - f_R) at every interface)
     nE = np.stack([np.cos(E * (k + 1)) for k in range(norb)], axis=1)            # [ne][orbitals]
     density = torch.from_numpy((w.numpy()[:, None] * nE).sum(0))
-    current = torch.from_numpy(np.repeat(np.exp(-E * E)[:, None], nb - 1, axis=1).reshape(-1).copy())
-    out = bench.energy_integrals(density, current, w, ne, nb, world)
+    T = torch.from_numpy(np.exp(-E * E))
+    fL = torch.from_numpy(1.0 / (1.0 + np.exp((E - 0.5) / 0.3)))
+    fR = torch.from_numpy(1.0 / (1.0 + np.exp((E + 0.5) / 0.3)))
+    J = (T * (fL - fR)).numpy()
+    current = torch.from_numpy(np.repeat(J[:, None], nb - 1, axis=1).reshape(-1).copy())
+    out = bench.energy_integrals(density, current, T, fL, fR, w, ne, nb, world)
     q.put((rank, out))
     dist.destroy_process_group()
 
@@ -156,12 +160,13 @@ def test_energy_integrals_sum_over_two_gloo_ranks():
         assert p.exitcode == 0
     grid = np.linspace(-3.0, 3.0, 32)
     dens_ref = sum(np.trapezoid(np.cos(grid * (k + 1)), grid) for k in range(3))
-    cur_ref = np.trapezoid(np.exp(-grid * grid), grid)
+    f = lambda mu: 1.0 / (1.0 + np.exp((grid - mu) / 0.3))
+    cur_ref = np.trapezoid(np.exp(-grid * grid) * (f(0.5) - f(-0.5)), grid)
     for _, out in res:
         assert out["collective"] == "all_reduce sum over 2 ranks"
         assert abs(out["density_total"] - dens_ref) < 1e-12
-        assert abs(out["current_mean"] - cur_ref) < 1e-12
-        assert out["current_spread"] < 1e-12
+        for k in ("current_interface_first", "current_interface_last", "current_landauer"):
+            assert abs(out[k] - cur_ref) < 1e-12
 
 
 def test_rank_weights_one_rank_is_the_local_trapezoid():
