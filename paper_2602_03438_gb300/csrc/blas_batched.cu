@@ -131,7 +131,7 @@ __device__ __forceinline__ typename CT<R>::T cmk(R a, R b) {
   typename CT<R>::T v; v.x = a; v.y = b; return v;
 }
 
-constexpr int kInvThreads = 512;
+constexpr int kInvThreads = 1024;
 
 // Work split: thread t owns column c = t mod n and rows r0, r0 + rs, ... with
 // r0 = t div n, rs = kInvThreads div n (threads beyond rs * n only help with the

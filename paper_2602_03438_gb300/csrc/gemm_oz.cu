@@ -1287,8 +1287,12 @@ constexpr uint32_t SMEM_P = 2 * STAGE_P + PAIR_BYTES + 1024 + 128;
 constexpr int NT_P = 18 * 32;
 constexpr int CL_P = 4;
 
-template <int CL>
-__global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages im, int* err, int unit_alpha_beta) {
+// UAB: alpha = +-1 and beta in {0, +-1} (sign flips and additions only); a template
+// parameter, so that the general complex alpha, beta arithmetic is not compiled into the
+// same predicated FP64 sequence
+template <int CL, bool UAB>
+__global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages im, int* err) {
+  constexpr bool unit_alpha_beta = UAB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int4* pairs = reinterpret_cast<int4*>(base + 2 * STAGE_P);
@@ -1688,14 +1692,19 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = once_per_device(INIT_OZP, [&cfg](int d) {
-    cudaError_t r = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t r = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_P);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_P);
     if (r != cudaSuccess) return r;
     cudaLaunchConfig_t q = cfg;
     q.gridDim = dim3(CL_P, 1, 1);
-    int ncl = 0;
-    r = cudaOccupancyMaxActiveClusters(&ncl, zgemm_ozp_kernel<CL_P>, &q);
+    int ncl = 0, ncl2 = 0;
+    r = cudaOccupancyMaxActiveClusters(&ncl, zgemm_ozp_kernel<CL_P, true>, &q);
+    if (r == cudaSuccess) r = cudaOccupancyMaxActiveClusters(&ncl2, zgemm_ozp_kernel<CL_P, false>, &q);
     if (r != cudaSuccess) return r;
+    ncl = std::min(ncl, ncl2);
     if (ncl < 1) return cudaErrorInvalidConfiguration;
     g_ozp_clusters[d] = ncl;
     return cudaSuccess;
@@ -1726,7 +1735,8 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
                           ? 1 : 0;
   const int ncl = g.units < max_clusters ? g.units : max_clusters;
   cfg.gridDim = dim3(ncl * CL_P, 1, 1);
-  e = cudaLaunchKernelEx(&cfg, zgemm_ozp_kernel<CL_P>, g, im, err, unit_ab);
+  e = unit_ab ? cudaLaunchKernelEx(&cfg, zgemm_ozp_kernel<CL_P, true>, g, im, err)
+              : cudaLaunchKernelEx(&cfg, zgemm_ozp_kernel<CL_P, false>, g, im, err);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
