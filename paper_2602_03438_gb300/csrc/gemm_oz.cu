@@ -217,6 +217,19 @@ __device__ __forceinline__ int scale_exp(double v) {
   return e + 1;
 }
 
+// The high word of |x| (sign cleared): for non-negative doubles it orders like the value
+// and carries its exponent field, so the largest entry's scale comes from integer maxima
+// (GB300's FP64 pipe is narrow; fabs/fmax per entry held the pre-pass on it).
+__device__ __forceinline__ unsigned int abs_hi(double x) { return (unsigned int)__double2hiint(x) & 0x7FFFFFFFu; }
+// scale_exp of the largest |entry| from the largest abs_hi word: the same exponent for a
+// normal maximum (frexp's e + 1 = exponent field - 1021), 0 for an all-zero vector, and
+// -1021 for a subnormal maximum (|x| < 2^(e - 1) still holds)
+__device__ __forceinline__ int scale_exp_hi(unsigned int h) {
+  if (h == 0) return 0;
+  const int ex = (int)(h >> 20);
+  return (ex == 0 ? 1 : ex) - 1021;
+}
+
 // sum of 64 in each of the NS - 1 low 7-bit fields (the balancing constant below)
 __host__ __device__ constexpr unsigned long long balance_constant(int fields) {
   return fields == 0 ? 0ull : (64ull << (7 * (fields - 1))) + balance_constant(fields - 1);
@@ -315,22 +328,22 @@ __global__ void oz_scale_kernel(GemmArgs g, int* ea, int* eb, int first) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (contiguous) {
     for (int r = warp; r < n; r += blockDim.x >> 5) {
-      double v = 0.0;
+      unsigned int v = 0;
       for (int k = lane; k < n; k += 32) {
         const zc x = M[(size_t)r * n + k];
-        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        v = max(v, max(abs_hi(x.x), abs_hi(x.y)));
       }
-      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
-      if (lane == 0) out[r] = scale_exp(v);
+      for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, off));
+      if (lane == 0) out[r] = scale_exp_hi(v);
     }
   } else {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      double v = 0.0;
+      unsigned int v = 0;
       for (int k = 0; k < n; ++k) {
         const zc x = M[(size_t)k * n + c];
-        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        v = max(v, max(abs_hi(x.x), abs_hi(x.y)));
       }
-      out[c] = scale_exp(v);
+      out[c] = scale_exp_hi(v);
     }
   }
 }
@@ -991,28 +1004,28 @@ __device__ __forceinline__ void b_col_scales(const ARGS& g, int u, int* eb) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (g.opB == OP_H) {
     for (int r = warp; r < n; r += 8) {
-      double v = 0.0;
+      unsigned int v = 0;
       for (int k = lane; k < n; k += 32) {
         const zc x = B[(size_t)r * n + k];
-        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        v = max(v, max(abs_hi(x.x), abs_hi(x.y)));
       }
-      for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
-      if (lane == 0) out[r] = scale_exp(v);
+      for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, off));
+      if (lane == 0) out[r] = scale_exp_hi(v);
     }
   } else {
-    __shared__ double bpart[2][128];
+    __shared__ unsigned int bpart[2][128];
     const int c = tid & 127, h = tid >> 7;
-    double v = 0.0;
+    unsigned int v = 0;
     if (c < n) {
 #pragma unroll 8
       for (int k = h; k < n; k += 2) {
         const zc x = B[(size_t)k * n + c];
-        v = fmax(v, fmax(fabs(x.x), fabs(x.y)));
+        v = max(v, max(abs_hi(x.x), abs_hi(x.y)));
       }
     }
     bpart[h][c] = v;
     __syncthreads();
-    if (tid < n) out[tid] = scale_exp(fmax(bpart[0][tid], bpart[1][tid]));
+    if (tid < n) out[tid] = scale_exp_hi(max(bpart[0][tid], bpart[1][tid]));
   }
 }
 
@@ -1053,14 +1066,14 @@ __global__ void __launch_bounds__(256) oz_digitize_a2_kernel(ARGS g, OzImages im
       v[j][h] = x;
     }
   }
-  double mx = 0.0;
+  unsigned int mh = 0;
 #pragma unroll
   for (int j = 0; j < PRE_OWN; ++j)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) mx = fmax(mx, fmax(fabs(v[j][h].x), fabs(v[j][h].y)));
+    for (int h = 0; h < 2; ++h) mh = max(mh, max(abs_hi(v[j][h].x), abs_hi(v[j][h].y)));
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  const int e = scale_exp(mx);
+  for (int off = 1; off < 8; off <<= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, off));
+  const int e = scale_exp_hi(mh);
   if (sub == 0 && gm < n) im.ea[(size_t)u * n + gm] = e;
 #pragma unroll
   for (int j = 0; j < PRE_OWN; ++j) {
