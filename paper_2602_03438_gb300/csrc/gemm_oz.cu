@@ -300,15 +300,28 @@ __device__ __forceinline__ void halves(const uint32_t (&v)[NG][W], int j, long l
                   l);
 }
 
-// exact int64 (|v| < 2^53) times 2^p as an IEEE double: the exact conversion, then p
-// added to the exponent field with one integer addition (0 when v = 0 or the result
-// would fall below the normal range, far below the tile's FP64-class accuracy)
+// int64 v (|v| < 2^62) times 2^p as an IEEE double: the conversion to nearest, then p added
+// to the exponent field with one integer addition (0 when v = 0 or the result would
+// fall below the normal range, far below the tile's FP64-class accuracy)
 __device__ __forceinline__ double ldexp_int(long long v, int p) {
-  const double x = __ll2double_rn(v);   // exact: |v| < 2^53
+  const double x = __ll2double_rn(v);
   const int hi = __double2hiint(x);
   const int e = ((hi >> 20) & 0x7FF) + p;
   if (v == 0 || e <= 0) return 0.0;
   return __hiloint2double(hi + (int)((unsigned)p << 20), __double2loint(x));
+}
+
+// The double nearest to (h 2^SH + l) 2^p for the two exact halves of an element's group
+// sums (|h|, |l| < 2^46, SH = 7 (NG - HSPLIT)): both are shifted down by s so that the
+// sum fits in 62 bits (s <= 13; the bits of l dropped by the shift lie more than 8 bits
+// below the sum's last significant bit), then one conversion.  One FP64-pipe operation
+// per value instead of two conversions and an addition (GB300's FP64 pipe is narrow).
+__device__ __forceinline__ double rebuild(long long h, long long l, int p) {
+  constexpr int SH = 7 * (NG - HSPLIT);
+  const unsigned long long ah = h < 0 ? 0ull - (unsigned long long)h : (unsigned long long)h;
+  const int s = max(0, (64 - __clzll((long long)ah)) + SH - 61);
+  const long long v = h * (1ll << (SH - s)) + (l >> s);
+  return ldexp_int(v, p + s);
 }
 
 // ---------------------------------------------------------------------------
@@ -594,9 +607,7 @@ __global__ void __launch_bounds__(NT + 64, 1) zgemm_oz_kernel(GemmArgs g, const 
           const int gcol = n0 + j0 + j;
           if (gcol < n) {
             const int p = er + eB[gcol] - 7 * (NS + 1);     // scale of the last group
-            const int ph = p + 7 * (NG - HSPLIT);           // scale of group HSPLIT-1
-            zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
-                           ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            zc acc = zmake(rebuild(hre[j], lre[j], p), rebuild(him[j], lim[j], p));
             zc v;
             if (unit_alpha_beta) {
               // alpha = +-1, beta in {0, +-1}: signs only, one FP64 add
@@ -905,9 +916,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
           const int gcol = n0 + j0 + j;
           if (gcol < n) {
             const int p = er + eB[gcol] - 7 * (NS + 1);
-            const int ph = p + 7 * (NG - HSPLIT);
-            const zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
-                                 ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            const zc acc = zmake(rebuild(hre[j], lre[j], p), rebuild(him[j], lim[j], p));
             zc v;
             if (unit_alpha_beta) {
               v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
@@ -1249,9 +1258,7 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
           const int gcol = n0 + j0 + j;
           if (gcol < n) {
             const int p = er + eB[gcol] - 7 * (NS + 1);
-            const int ph = p + 7 * (NG - HSPLIT);
-            const zc acc = zmake(ldexp_int(hre[j], ph) + ldexp_int(lre[j], p),
-                                 ldexp_int(him[j], ph) + ldexp_int(lim[j], p));
+            const zc acc = zmake(rebuild(hre[j], lre[j], p), rebuild(him[j], lim[j], p));
             zc v;
             if (unit_alpha_beta) {
               v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
@@ -1549,8 +1556,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
             halves_of_pairs(qr.x, qr.y, qr.z, qr.w, hr, lr);
             halves_of_pairs(qi.x, qi.y, qi.z, qi.w, hi, li);
             const int p = er + ebv[j];
-            const int ph = p + 7 * (NG - HSPLIT);
-            const zc acc = zmake(ldexp_int(hr, ph) + ldexp_int(lr, p), ldexp_int(hi, ph) + ldexp_int(li, p));
+            const zc acc = zmake(rebuild(hr, lr, p), rebuild(hi, li, p));
             zc v;
             if (unit_alpha_beta) {
               v = (g.alpha.x < 0) ? zmake(-acc.x, -acc.y) : acc;
