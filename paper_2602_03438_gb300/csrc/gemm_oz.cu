@@ -620,6 +620,7 @@ __global__ void __launch_bounds__(NT + 64, 1) zgemm_oz_kernel(GemmArgs g, const 
               v = zmul(g.alpha, acc);
               if (Cm) v = zadd(v, zmul(g.beta, Cm[(size_t)row * n + gcol]));
             }
+            if (g.plus_identity && row == gcol) v.x += 1.0;
             D[(size_t)row * n + gcol] = v;
           }
         }
@@ -928,6 +929,7 @@ __global__ void __launch_bounds__(NT_T, 1) zgemm_ozt_kernel(GemmArgs g, OzImages
               v = zmul(g.alpha, acc);
               if (Cm) v = zadd(v, zmul(g.beta, Cm[(size_t)row * n + gcol]));
             }
+            if (g.plus_identity && row == gcol) v.x += 1.0;
             D[(size_t)row * n + gcol] = v;
           }
         }
@@ -1270,6 +1272,7 @@ __global__ void __launch_bounds__(NT2, 2) zgemm_ozs_kernel(GemmArgs g, OzImages 
               v = zmul(g.alpha, acc);
               if (Cm) v = zadd(v, zmul(g.beta, Cm[(size_t)row * n + gcol]));
             }
+            if (g.plus_identity && row == gcol) v.x += 1.0;
             D[(size_t)row * n + gcol] = v;
           }
         }
@@ -1503,6 +1506,13 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
     uint32_t tiles = 0;
     for (int u = cid; u < g.units && !s_fail; u += ncl) {
       if (skip(u)) continue;
+      // this thread's C row segment (16 complex, two 128-byte lines) into L1 while the
+      // MMAs run, so that the rebuild does not wait on L2 for it
+      if (g.C.p && rl < n && n0 + cbase < n) {
+        const zc* crow = g.C.at(u) + (size_t)rl * n + n0 + cbase;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow) : "memory");
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(crow + 8) : "memory");
+      }
       if (!mbar_wait(done, tiles & 1)) { s_fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // phase 1: TMEM -> exact int32 group pairs in shared memory (this lane's row)
@@ -1565,6 +1575,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
               v = zmul(g.alpha, acc);
               if (Cm) v = zadd(v, zmul(g.beta, cv[j]));
             }
+            if (g.plus_identity && row == gcol) v.x += 1.0;
             D[(size_t)row * n + gcol] = v;
           }
         }
@@ -1836,6 +1847,7 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
     if (c0 > 0) {
       gp.C = g.D;
       gp.beta = zmake(1.0, 0.0);
+      gp.plus_identity = 0;   // added once, by the first pass
     }
     im.c_begin = c0;
     im.c_count = (im.nchunks - c0) < per_pass ? (im.nchunks - c0) : per_pass;

@@ -515,8 +515,13 @@ struct Engine {
       r.opA = OP_N; r.opB = OP_N; r.alpha = zmake(1.0, 0.0); r.beta = zmake(0.0, 0.0);
       r.n = n; r.units = units; r.active = active;
       const double frac = (active && active_frac >= 0.0) ? active_frac : 1.0;
-      // M X with FP64-class accuracy: the sliced tensor-core product, else FP64 FMA
-      if (mixed == 1 && can_slice(n)) {
+      // I - M X with FP64-class accuracy: the sliced tensor-core product with alpha = -1
+      // and the identity added in its epilogue (the same FP64 operation 1 - (M X)_kk),
+      // else M X by FP64 FMA and I - M X in a pass of its own
+      const bool fused = mixed == 1 && can_slice(n);
+      if (fused) {
+        r.alpha = zmake(-1.0, 0.0);
+        r.plus_identity = 1;
         begin(K_GEMM_OZ);
         e = sliced(r);
       } else {
@@ -525,9 +530,11 @@ struct Engine {
       }
       end(8.0 * (double)n * n * n * units * frac, 48.0 * (double)n * n * units * frac);
       if (e != cudaSuccess) return e;
-      ++ctx->launches;
-      one_minus_kernel<<<grid, 256, 0, s>>>(T1, n, active);               // I - M X
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (!fused) {
+        ++ctx->launches;
+        one_minus_kernel<<<grid, 256, 0, s>>>(T1, n, active);             // I - M X
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
       if (mixed == 1 && ozt_scratch && oz_supported(n)) {
         // X <- X + X (I - M X) in one product: these kernels read op(A) only through the
         // digit images made before they start, and C and D element by element in one

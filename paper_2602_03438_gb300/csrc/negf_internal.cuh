@@ -75,6 +75,7 @@ struct GemmArgs {
   int n;               // matrix size
   int units;           // batch
   const int* active;   // per unit, nullable: 0 => unit skipped
+  int plus_identity = 0;   // sliced kernels: D += I after the rest (the residual I - M X in one product)
 };
 
 // ---------------------------------------------------------------------------
