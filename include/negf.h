@@ -416,11 +416,12 @@ int32_t negf_sliced_digits(void);
 negf_status negf_profile_enable(negf_ctx* ctx, int enable);
 /* Accumulated since the last reset: `launches` = all kernels this context has
  * launched; per kernel class k (0 = TF32-split GEMM, 1 = FP64 GEMM, 2 = FP32
- * inverse, 3 = FP64 inverse, 4 = other (masked launches), 5 = sliced BF16 GEMM)
+ * inverse, 3 = FP64 inverse, 4 = other (masked launches), 5 = sliced BF16 GEMM,
+ * 6 = sliced BF16 GEMM with 5 digits, the refinement's correction products)
  * the launches, total milliseconds,
  * algorithmic flops (8 n^3 per complex n x n product or inverse, times the
  * units) and algorithmic bytes (16 n^2 per operand read or written).  Each
- * array has 6 entries; any pointer may be NULL. */
+ * array has 7 entries; any pointer may be NULL. */
 negf_status negf_profile_read(negf_ctx* ctx, int64_t* launches, int64_t* k_launches, double* k_ms,
                               double* k_flops, double* k_bytes);
 negf_status negf_profile_reset(negf_ctx* ctx);

@@ -47,10 +47,19 @@ constexpr int KC = 16;                  // complex K per chunk
 #ifndef NEGF_OZ_DIGITS
 #define NEGF_OZ_DIGITS 8
 #endif
+// This file is compiled twice: with NEGF_OZ_DIGITS digits (8 by default) for every
+// FP64-class product, and with NEGF_OZ_LOW and 5 digits (gemm_oz_lo.cu) for products
+// whose result is a small correction (error ~2^-34 of the row x column norms); that
+// build exports zgemm_ozt_lo alone and keeps its own once-per-device set-up slots
+#ifdef NEGF_OZ_LOW
+#define OZ_SLOT(x) x##_LO
+#else
+#define OZ_SLOT(x) x
+#endif
 constexpr int NS = NEGF_OZ_DIGITS;      // digits per value
 constexpr int NG = NS;                  // scale groups d = 2..NS+1
 constexpr int HSPLIT = 4;               // groups [0, HSPLIT) and [HSPLIT, NG) recombine separately
-static_assert(NS >= 6 && NS <= 8, "6 to 8 digits: the group sums and the halves stay exact");
+static_assert(NS >= 4 && NS <= 8, "4 to 8 digits: the group sums and the halves stay exact");
 constexpr int NT = 256;
 constexpr int kCluster = 4;            // column tiles sharing one A tile's digits
 constexpr uint32_t ROWB = 64;                            // bytes per smem row (32 bf16)
@@ -1594,6 +1603,7 @@ __global__ void __launch_bounds__(NT_P, 1) zgemm_ozp_kernel(GemmArgs g, OzImages
 
 // exact group sums need NS * 64 * 64 * 2K <= 2^24 per accumulation (K <= 256 for NS <= 8): the in-kernel-digit
 // kernel accumulates the whole K (n <= 256); the digitize-once kernels run K in passes
+#ifndef NEGF_OZ_LOW
 bool oz_supported(int n) { return n >= 16 && n <= 512; }
 bool oz_inkernel_supported(int n) { return n >= 16 && n <= 256; }
 
@@ -1639,9 +1649,12 @@ cudaError_t zgemm_oz(const GemmArgs& g, void* scratch, int* err, cudaStream_t s)
   return cudaGetLastError();
 }
 
+#endif  // NEGF_OZ_LOW
+
 // digitize-once variants: scales + A digit images (the larger of the two layouts)
 static int ozt_tiles_n(int n) { return ((n + TNC - 1) / TNC + kCluster - 1) / kCluster * kCluster; }
 
+#ifndef NEGF_OZ_LOW
 size_t ozt_scratch_bytes(int n, int units) {
   const size_t tm = (size_t)(n + TM - 1) / TM;
   size_t b = sizeof(int) * 2 * (size_t)n * units;
@@ -1650,10 +1663,11 @@ size_t ozt_scratch_bytes(int n, int units) {
   b += (size_t)units * tm * (full > half ? full : half);
   return b;
 }
+#endif
 
 // half-width tiles, two CTAs per SM; cluster = the column tiles sharing one A image
 static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
-  cudaError_t e = once_per_device(INIT_OZS, [](int) {
+  cudaError_t e = once_per_device(OZ_SLOT(INIT_OZS), [](int) {
     cudaError_t r = cudaFuncSetAttribute(zgemm_ozs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
     if (r == cudaSuccess) r = cudaFuncSetAttribute(zgemm_ozs_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
     if (r == cudaSuccess) r = cudaFuncSetAttribute(zgemm_ozs_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2);
@@ -1721,7 +1735,7 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  e = once_per_device(INIT_OZP, [&cfg](int d) {
+  e = once_per_device(OZ_SLOT(INIT_OZP), [&cfg](int d) {
     cudaError_t r = cudaFuncSetAttribute(zgemm_ozp_kernel<CL_P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_P);
     if (r == cudaSuccess)
@@ -1774,6 +1788,7 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
 // full-width tiles (one CTA per SM)
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 
+#ifndef NEGF_OZ_LOW
 bool oz_variant_supported(int n, int variant) {
   if (!oz_supported(n)) return false;
   switch (variant) {
@@ -1799,12 +1814,23 @@ cudaError_t zgemm_ozt_variant(const GemmArgs& g, void* scratch, int* err, cudaSt
 cudaError_t zgemm_ozt(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
   return zgemm_ozt_variant(g, scratch, err, s, OZ_DEFAULT);
 }
+#else
+// the low-digit product with the default tile rule (the images of its 5 digit planes fit
+// in the scratch sized for the full product)
+cudaError_t zgemm_ozt_lo(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
+  if (g.units <= 0 || g.n <= 0) return cudaSuccess;
+  if (!scratch || g.n < 16 || g.n > 512) return cudaErrorInvalidValue;
+  if (g.n <= 96) return zgemm_ozs(g, scratch, err, s);
+  if (g.n <= 128) return zgemm_ozp(g, scratch, err, s);
+  return zgemm_ozt_full(g, scratch, err, s);
+}
+#endif
 
 static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cudaStream_t s) {
   if (g.units <= 0 || g.n <= 0) return cudaSuccess;
   if (!scratch) return cudaErrorInvalidValue;
   constexpr int CL = kCluster;
-  cudaError_t e = once_per_device(INIT_OZT, [](int) {
+  cudaError_t e = once_per_device(OZ_SLOT(INIT_OZT), [](int) {
     return cudaFuncSetAttribute(zgemm_ozt_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (e != cudaSuccess) return e;
@@ -1863,4 +1889,6 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
 
 }  // namespace negf
 
+#ifndef NEGF_OZ_LOW
 extern "C" int32_t negf_sliced_digits(void) { return negf::NS; }
+#endif

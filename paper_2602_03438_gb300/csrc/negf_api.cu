@@ -538,9 +538,19 @@ struct Engine {
       if (mixed == 1 && ozt_scratch && oz_supported(n)) {
         // X <- X + X (I - M X) in one product: these kernels read op(A) only through the
         // digit images made before they start, and C and D element by element in one
-        // thread, so D, A and C may all be X
-        if ((e = gemm(X, X, OP_N, T1, OP_N, zmake(1.0, 0.0), X, zmake(1.0, 0.0), n, units, active)) != cudaSuccess)
-          return e;
+        // thread, so D, A and C may all be X.  I - M X is small (below ~1e-3 when the
+        // FP32 inverse is usable at all), so the correction X (I - M X) needs far less
+        // than FP64 class: the 5-digit product (15 slice pairs instead of 36, error
+        // ~2^-34 of |X| |I - M X|; 4 digits measured G^R 9e-8 against FP64 at config 2)
+        GemmArgs c;
+        c.D = X; c.A = X; c.B = T1; c.C = X;
+        c.opA = OP_N; c.opB = OP_N; c.alpha = zmake(1.0, 0.0); c.beta = zmake(1.0, 0.0);
+        c.n = n; c.units = units; c.active = active;
+        const bool masked = active != nullptr && active_frac < 0.0;
+        begin(masked ? K_OTHER : K_GEMM_OZ_LO);
+        e = zgemm_ozt_lo(c, ozt_scratch, ctx->d_err, s);
+        end(masked ? 0.0 : 8.0 * (double)n * n * n * units * frac, masked ? 0.0 : 64.0 * (double)n * n * units * frac);
+        if (e != cudaSuccess) return e;
         continue;
       }
       if ((e = gemm(T2, X, OP_N, T1, OP_N, zmake(1.0, 0.0), BMat{nullptr, 0}, zmake(0.0, 0.0), n, units, active)) !=

@@ -19,7 +19,8 @@ namespace negf {
 // current, under a process-wide lock, at most once per (device, slot); a failed init
 // is not recorded, so the next call retries it.
 // ---------------------------------------------------------------------------
-enum InitSlot { INIT_OZ = 0, INIT_OZS, INIT_OZP, INIT_OZT, INIT_TC, INIT_MLP, INIT_NSLOT };
+enum InitSlot { INIT_OZ = 0, INIT_OZS, INIT_OZP, INIT_OZT, INIT_TC, INIT_MLP, INIT_OZS_LO, INIT_OZP_LO, INIT_OZT_LO,
+                INIT_NSLOT };
 constexpr int kMaxDevices = 64;
 cudaError_t once_per_device(int slot, const std::function<cudaError_t(int device)>& init);
 
@@ -82,7 +83,8 @@ struct GemmArgs {
 // library context
 // ---------------------------------------------------------------------------
 // kernel classes of the timing facility (negf_profile_*)
-enum KClass { K_GEMM_TC = 0, K_GEMM_F64 = 1, K_INV_F32 = 2, K_INV_F64 = 3, K_OTHER = 4, K_GEMM_OZ = 5, K_NCLASS = 6 };
+enum KClass { K_GEMM_TC = 0, K_GEMM_F64 = 1, K_INV_F32 = 2, K_INV_F64 = 3, K_OTHER = 4, K_GEMM_OZ = 5, K_GEMM_OZ_LO = 6,
+              K_NCLASS = 7 };
 
 struct ProfRec {
   int cls;
@@ -103,10 +105,10 @@ struct Ctx {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   int oz_variant[513] = {0};    // tile variant of the sliced product per block size (autotuner)
-  long long k_launches[K_NCLASS] = {0, 0, 0, 0, 0, 0};
-  double k_ms[K_NCLASS] = {0, 0, 0, 0, 0, 0};
-  double k_flops[K_NCLASS] = {0, 0, 0, 0, 0, 0};
-  double k_bytes[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  long long k_launches[K_NCLASS] = {};
+  double k_ms[K_NCLASS] = {};
+  double k_flops[K_NCLASS] = {};
+  double k_bytes[K_NCLASS] = {};
   cudaEvent_t take_event() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e = nullptr;
@@ -127,6 +129,9 @@ __device__ __forceinline__ void raise_error(int* err, int code) {
 cudaError_t zgemm_f64(const GemmArgs& g, cudaStream_t s);
 // 3-term TF32-split complex GEMM on tcgen05 tensor cores (FP32 accumulate in TMEM)
 cudaError_t zgemm_tc(const GemmArgs& g, int* err, cudaStream_t s);
+// the sliced product with 5 digits per value (error ~2^-34 of the row x column norms),
+// for products whose result is a small correction; scratch as for zgemm_ozt (16 <= n <= 512)
+cudaError_t zgemm_ozt_lo(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
 bool tc_supported(int n);
 // FP64-class complex GEMM on the BF16 tensor cores (exact-accumulation digit slices);
 // `scratch` holds oz_scratch_bytes(n, units) bytes of per-row/column scales

@@ -37,7 +37,7 @@ EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_s
            "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
            "negf_mlp_forward", "negf_mlp_train_step", "negf_sliced_digits", "negf_tune_products",
            "negf_set_product_variant"]
-KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz"]
+KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz", "gemm_oz_lo"]
 
 
 class NegfError(RuntimeError):

@@ -1,7 +1,8 @@
 """The balanced base-2^7 digit split behind the sliced tensor-core products, on the host.
 
 The product kernels cut each scaled entry X = rint(|x| 2^(7 NS - e)) <= 2^(7 NS - 1) into
-NS digits d_(NS-1)..d_0 (NS = 6, 7 or 8; 7 by default) with X = sum_k d_k 2^(7k),
+NS digits d_(NS-1)..d_0 (NS = 8 by default, 6 or 7 as a build parameter, 5 for the
+refinement's correction products; 4 still exact) with X = sum_k d_k 2^(7k),
 |d_k| <= 64 for the low digits, so that each digit is exact in BF16 and every slice
 product is exact in FP32.  They form the digits with one addition: adding 64 to each of
 the NS - 1 low 7-bit fields lets the binary carries do the balancing (field k of
@@ -23,7 +24,7 @@ def _set_ns(ns):
     BAL = sum(64 << (7 * k) for k in range(NS - 1))
 
 
-@pytest.fixture(params=[6, 7, 8], autouse=True)
+@pytest.fixture(params=[4, 5, 6, 7, 8], autouse=True)
 def digit_count(request):
     _set_ns(request.param)
     yield request.param
@@ -61,7 +62,8 @@ def _cases():
 
 def test_balancing_constant():
     # the constants the kernels add: 64 in each of the NS - 1 low 7-bit fields
-    assert BAL == {6: 0x0000000408102040, 7: 0x0000020408102040, 8: 0x0001020408102040}[NS]
+    assert BAL == {4: 0x0000000000102040, 5: 0x0000000008102040, 6: 0x0000000408102040, 7: 0x0000020408102040,
+                   8: 0x0001020408102040}[NS]
 
 
 def test_addition_matches_carry_loop_and_definition():
