@@ -426,6 +426,17 @@ negf_status negf_profile_read(negf_ctx* ctx, int64_t* launches, int64_t* k_launc
                               double* k_flops, double* k_bytes);
 negf_status negf_profile_reset(negf_ctx* ctx);
 
+/* Failure-detection self test (not a paper operation).  Launches one CTA whose thread
+ * waits, with the bounded device wait every tensor-core kernel of this library uses (an
+ * mbarrier try_wait loop limited by %globaltimer), on an mbarrier that nothing arrives
+ * on; after `wait_ns` of GPU time (1e6 <= wait_ns <= 2e9) the wait gives up and the
+ * kernel raises NEGF_ERR_TIMEOUT on the context, exactly as a product kernel whose
+ * operands never arrive would, and returns.  No copy, MMA or other CTA is in flight, so
+ * the context stays usable; the next negf_ctx_sync(ctx, stream) returns
+ * NEGF_ERR_TIMEOUT and clears it.  Returns NEGF_OK once launched, NEGF_ERR_ARG for a
+ * budget out of range, NEGF_ERR_CUDA if the launch fails. */
+negf_status negf_selftest_wait_timeout(negf_ctx* ctx, int64_t wait_ns, negf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

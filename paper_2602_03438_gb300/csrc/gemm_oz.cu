@@ -127,16 +127,17 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
-// bounded wait: gives up after kWaitNs of GPU time (the caller records the timeout)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: gives up after `limit_ns` of GPU time (the caller records the timeout)
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   unsigned long long t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > kWaitNs) return false;
+    if (t - t0 > limit_ns) return false;
   }
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_ns(bar, parity, kWaitNs); }
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -1891,4 +1892,24 @@ static cudaError_t zgemm_ozt_full(const GemmArgs& g, void* scratch, int* err, cu
 
 #ifndef NEGF_OZ_LOW
 extern "C" int32_t negf_sliced_digits(void) { return negf::NS; }
+
+namespace negf {
+namespace {
+// The failure-detection self test: one thread waits, with the product kernels' bounded
+// wait, on an mbarrier that nothing arrives on, so that the wait runs out after
+// `limit_ns`; it then raises NEGF_ERR_TIMEOUT on the context's error word.  Nothing
+// else (no bulk copy, no MMA, no other CTA) is in flight.
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_ns(&bar, 0u, limit_ns)) raise_error(err, NEGF_ERR_TIMEOUT);
+}
+}  // namespace
+
+cudaError_t wait_selftest(int* err, unsigned long long limit_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+}  // namespace negf
 #endif

@@ -2739,6 +2739,17 @@ negf_status negf_profile_read(negf_ctx* c, int64_t* launches, int64_t* k_launche
   return NEGF_OK;
 }
 
+negf_status negf_selftest_wait_timeout(negf_ctx* c, int64_t wait_ns, negf_stream stream) {
+  Ctx* ctx = reinterpret_cast<Ctx*>(c);
+  if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");
+  if (wait_ns < 1000000 || wait_ns > 2000000000)
+    return fail(ctx, NEGF_ERR_ARG, "wait_ns must lie in [1e6, 2e9]");
+  CU(cudaSetDevice(ctx->device));
+  ++ctx->launches;
+  CU(wait_selftest(ctx->d_err, (unsigned long long)wait_ns, (cudaStream_t)stream));
+  return NEGF_OK;
+}
+
 negf_status negf_profile_reset(negf_ctx* c) {
   Ctx* ctx = reinterpret_cast<Ctx*>(c);
   if (!ctx) return fail(nullptr, NEGF_ERR_ARG, "ctx is NULL");

@@ -132,6 +132,8 @@ cudaError_t zgemm_tc(const GemmArgs& g, int* err, cudaStream_t s);
 // the sliced product with 5 digits per value (error ~2^-34 of the row x column norms),
 // for products whose result is a small correction; scratch as for zgemm_ozt (16 <= n <= 512)
 cudaError_t zgemm_ozt_lo(const GemmArgs& g, void* scratch, int* err, cudaStream_t s);
+// one bounded device wait that runs out after limit_ns and raises NEGF_ERR_TIMEOUT on err
+cudaError_t wait_selftest(int* err, unsigned long long limit_ns, cudaStream_t s);
 bool tc_supported(int n);
 // FP64-class complex GEMM on the BF16 tensor cores (exact-accumulation digit slices);
 // `scratch` holds oz_scratch_bytes(n, units) bytes of per-row/column scales

@@ -36,7 +36,7 @@ EXPORTS = ["negf_ctx_create", "negf_ctx_destroy", "negf_last_error", "negf_ctx_s
            "negf_profile_read", "negf_profile_reset", "negf_block_gemm", "negf_block_inverse",
            "negf_block_gemm_noalloc", "negf_mlp_get_dims", "negf_mlp_workspace_bytes", "negf_mlp_pack",
            "negf_mlp_forward", "negf_mlp_train_step", "negf_sliced_digits", "negf_tune_products",
-           "negf_set_product_variant"]
+           "negf_set_product_variant", "negf_selftest_wait_timeout"]
 KERNEL_CLASSES = ["gemm_tc", "gemm_f64", "inv_f32", "inv_f64", "other", "gemm_oz", "gemm_oz_lo"]
 
 
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.negf_sliced_digits.argtypes = []
     lib.negf_tune_products.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(dbl), vp]
     lib.negf_set_product_variant.argtypes = [vp, i32, i32]
+    lib.negf_selftest_wait_timeout.argtypes = [vp, C.c_int64, vp]
     for name in EXPORTS:
         if name not in ("negf_last_error", "negf_mlp_workspace_bytes"):
             getattr(lib, name).restype = C.c_int
@@ -193,6 +194,11 @@ class Context:
     def sync(self, stream=None) -> int:
         """Synchronize the stream; returns the worst device-side status (0 = OK)."""
         return int(self.lib.negf_ctx_sync(self.h, _stream(stream)))
+
+    def selftest_wait_timeout(self, wait_ns: int, stream=None):
+        """Launch the failure-detection self test: one bounded device wait that runs
+        out after wait_ns and raises NEGF_ERR_TIMEOUT (read it with sync())."""
+        self.check(self.lib.negf_selftest_wait_timeout(self.h, int(wait_ns), _stream(stream)))
 
 
 @dataclass
