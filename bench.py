@@ -432,8 +432,9 @@ def run_gpu(args):
 
     # ---- FP64 comparison on a bounded subset of the energies (same device, same Sigma)
     cmp = {}
-    if args.fp64_sample > 0 and rank == 0:
-        k = min(args.fp64_sample, ne)
+    fp64_sample = 128 if args.fp64_sample is None else args.fp64_sample
+    if fp64_sample > 0 and rank == 0:
+        k = min(fp64_sample, ne)
         idx = np.linspace(0, ne - 1, k).round().astype(int)
         sub = W.config2(nb=args.nb, b=args.b, ne=args.ne)
         sub.energy = dev.energy[idx]
@@ -681,7 +682,7 @@ def run_config4(args):
         raise RuntimeError("device status after the config-4 run")
     ms_obc, ms_sw = e0.elapsed_time(e1), e1.elapsed_time(e2)
     # FP64 sweeps with stored blocks on sampled energies, same Sigma
-    k = max(1, min(args.fp64_sample, dev.ne))
+    k = max(1, min(4 if args.fp64_sample is None else args.fp64_sample, dev.ne))
     idx = np.linspace(0, dev.ne - 1, k).round().astype(int)
     sub = dev.truncated(energies=idx)
     s2 = P.upload(sub)
@@ -778,7 +779,7 @@ def run_workload(args):
     L = sys_.layout()
     subs, idx_all = [], []
     for d, dev in enumerate(devs):
-        k = min(args.fp64_sample, dev.ne)
+        k = min(1 if args.fp64_sample is None else args.fp64_sample, dev.ne)
         idx = np.linspace(0, dev.ne - 1, k).round().astype(int)
         subs.append(dev.truncated(energies=idx))
         idx_all.append((d, idx))
@@ -849,7 +850,9 @@ def main(argv=None):
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--ne", type=int, default=1024)
     ap.add_argument("--workspace-gb", type=float, default=24.0)
-    ap.add_argument("--fp64-sample", type=int, default=64)
+    ap.add_argument("--fp64-sample", type=int, default=None,
+                    help="energies per device of the FP64 comparison (default: 128 for the bench line, "
+                         "4 for --workload config4, 1 for --workload config3)")
     ap.add_argument("--ref-energies", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
