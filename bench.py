@@ -441,6 +441,11 @@ def run_gpu(args):
     if fp64_sample > 0 and rank == 0:
         k = min(fp64_sample, ne)
         idx = np.linspace(0, ne - 1, k).round().astype(int)
+        # and the energy where the mixed current peaks, so that the error floor of the
+        # current (1e-3 of its largest value over the grid) is itself checked against FP64
+        j_peak = int(out["current"].view(ne, nb - 1).abs().amax(dim=1).argmax().item())
+        idx = np.unique(np.append(idx, j_peak))
+        k = int(idx.size)
         sub = W.config2(nb=args.nb, b=args.b, ne=args.ne)
         sub.energy = dev.energy[idx]
         s2 = P.upload(sub)
@@ -478,7 +483,7 @@ def run_gpu(args):
             den = torch.stack([dens[x] for x in keys]).amax(0).clamp_min(1e-300)
             joint[g] = float((num / den).max().item())
         obs_err = observables_vs_fp64(P, ctx, s2, o2, out, idx, w, ne, nb, b)
-        cmp = {"fp64_rgf_value": fp64_value, "fp64_energies": k, "speedup_vs_fp64": rgf_value / world / fp64_value,
+        cmp = {"fp64_rgf_value": fp64_value, "fp64_energies": k, "current_peak_energy_index": j_peak, "speedup_vs_fp64": rgf_value / world / fp64_value,
                "err_vs_fp64_max": max(max(joint.values()), obs_err["J"], obs_err["n"]), "err_vs_fp64": joint,
                "err_observables_vs_fp64": obs_err, "err_per_block_family": errs}
         del o2, s2
