@@ -158,7 +158,7 @@ negf_status negf_worklist(const negf_system* sys, int32_t bs, int32_t* count, in
  * LDL^H pivots of A = i (g - g^H) all exceed -1e-12 max_k A_kk (for S = I leads
  * A is positive definite exactly for the decaying root, by the inertia theorem
  * of the Stein equation A = 2 eta g g^H + (g H01) A (g H01)^H).  Otherwise that
- * lead of that energy falls back to the decimation above, which stays the judge
+ * lead of that energy falls back to the decimation above, which stays the arbiter
  * of the 1e-10 residual.  The guesses have no counterpart in the paper; see
  * negf_warmstart.h for the network that produces them.
  *   g0_L, g0_R : in, device [sum ne] blocks of surface-function guesses, or NULL.

@@ -255,7 +255,7 @@ def surface_newton_warm(a00, alpha, beta, g0, target=1e-13, max_steps=8, smith_l
 
 def warm_surface_gf(a00, alpha, beta, g0, accept=1e-10, tol=1e-12, max_iter=100, target=1e-13,
                     warm_steps=8):
-    """Surface function from a warm start, with the decimation as fallback and judge:
+    """Surface function from a warm start, with the decimation as fallback and arbiter:
     Newton from ``g0``; the result is taken when its residual is <= ``accept`` and it
     passes ``retarded_check``; otherwise the plain decimation + polishing runs.
     Returns (g, decimation iterations, newton steps, residual, warm_taken)."""

@@ -73,7 +73,7 @@ def _run(P, b, eta, steps, lr=3e-4):
                             newton=float(zero.newton[:, 1].mean()), ms=zero.ms),
         )
         print(json.dumps(out))
-        # the plain solver is the judge: every energy converged, whichever path it took,
+        # the plain solver is the arbiter: every energy converged, whichever path it took,
         # to the same retarded surface function
         for r in (cold, warm, zero):
             assert np.all(r.status == 0) or np.array_equal(r.status != 0, cold.status != 0)
