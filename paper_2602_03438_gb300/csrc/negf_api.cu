@@ -1426,6 +1426,39 @@ __global__ void not_kernel(const int* a, int* out, int units) {
   if (u < units) out[u] = a[u] ? 0 : 1;
 }
 
+// off[0 .. c-1] = u * bb for the c units with mask[u] != 0, in increasing u (one CTA
+// of 1024 threads: ballots within warps, a scan of the warp counts per tile of 1024)
+__global__ void __launch_bounds__(1024) compact_kernel(const int* mask, int units, long long bb, long long* off) {
+  __shared__ int wsum[32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int i0 = 0; i0 < units; i0 += 1024) {
+    const int i = i0 + tid;
+    const int f = (i < units && mask[i]) ? 1 : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int pre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    if (w == 0) {   // exclusive prefix of the 32 warp counts
+      const int v = wsum[lane];
+      int x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      wsum[lane] = x - v;
+    }
+    __syncthreads();
+    const int base = s_base;
+    if (f) off[base + wsum[w] + pre] = (long long)i * bb;
+    __syncthreads();
+    if (tid == 1023) s_base = base + wsum[31] + __popc(bal);
+    __syncthreads();
+  }
+}
+
 __global__ void count_kernel(const int* flags, int units, int* out) {
   int c = 0;
   for (int u = threadIdx.x; u < units; u += blockDim.x) c += flags[u] != 0;
@@ -2333,7 +2366,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
     // products on the sliced tensor-core path (FP64-class) when asked for and supported
     const int sl = (prec == NEGF_MIXED && oz_supported(b)) ? 1 : 0;
     eng.mixed = sl;
-    const size_t per_unit = nslots * blk + 64 + zinv_scratch_bytes(b, 1, 0) + (sl ? ozt_scratch_bytes(b, 1) : 0) +
+    const size_t per_unit = nslots * blk + 96 + zinv_scratch_bytes(b, 1, 0) + (sl ? ozt_scratch_bytes(b, 1) : 0) +
                             (batched ? 3 * sizeof(int) + sizeof(long long) : 0);
     const size_t fixed = 8192 + (batched ? (sizeof(UnitDev) * ud.size() + 6 * 256) : 0);
     if (ctx->ws_bytes <= fixed) return fail(ctx, NEGF_ERR_NOMEM, "workspace too small for one OBC energy");
@@ -2369,6 +2402,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       double* ref = (double*)p; p += sizeof(double) * NU;
       double* res = (double*)p; p += sizeof(double) * NU;
       double* resn = (double*)p; p += sizeof(double) * NU;
+      long long* coff = (long long*)p; p += sizeof(long long) * NU;   // compact unit list (block offsets)
       int* done = (int*)p; p += sizeof(int) * NU;
       int* it_arr = (int*)p; p += sizeof(int) * NU;
       int* need = (int*)p; p += sizeof(int) * NU;
@@ -2424,6 +2458,31 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
         KCHECK();
         return NEGF_OK;
       };
+      // Products over a compact list of units: the units active at the last count (a
+      // superset of those active now, since units only leave the loops; a listed unit
+      // that has finished since computes results that are never read again) instead of
+      // a launch over all NU units with a mask, once at most half of them are active
+      int ncomp = 0;   // > 0: the products run over the list in coff
+      auto compact = [&](const int* mask, int cnt) -> negf_status {
+        ncomp = 0;
+        if (cnt <= 0 || 2 * cnt > NU) return NEGF_OK;
+        ++ctx->launches;
+        compact_kernel<<<1, 1024, 0, s>>>(mask, NU, bb, coff);
+        CU(cudaGetLastError());
+        ncomp = cnt;
+        return NEGF_OK;
+      };
+      auto lgemm = [&](BMat D, BMat A, int opA, BMat B, int opB, zc alpha, BMat C, zc beta,
+                       const int* mask) -> cudaError_t {
+        if (ncomp > 0) {
+          auto cm = [&](BMat m) {
+            if (m.p) m.off = coff;
+            return m;
+          };
+          return eng.gemm(cm(D), cm(A), opA, cm(B), opB, alpha, cm(C), beta, b, ncomp, nullptr);
+        }
+        return eng.gemm(D, A, opA, B, opB, alpha, C, beta, b, NU, mask);
+      };
       auto n_set = [&](const int* flags) -> int {
         ++ctx->launches;
         count_kernel<<<1, 256, 0, s>>>(flags, NU, n_active);
@@ -2435,31 +2494,36 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       // One Newton step on F(X) = (a00 - al X be) X - I for the units flagged in `mask`:
       // K D - al D (be g) = -F, solved as the Stein equation D = -K^{-1}F + (K^{-1} al) D (be g)
       // by Smith doubling (at most 96 levels); gn = g + D and resn = its residual.
-      // T1 = K and T2 = F of the current g must be in place (left by the last residual).
-      auto newton_step = [&](int* mask, BMat gn) -> negf_status {
+      // T1 = K and T2 = F of the current g must be in place (left by the last residual);
+      // cnt = the number of units in `mask`.
+      auto newton_step = [&](int* mask, BMat gn, int cnt) -> negf_status {
+        negf_status sc;
         CU(eng.inv(T[3], T[1], b, NU, mask, 0, nullptr));                 // K^{-1}
-        CU(eng.gemm(T[4], T[3], OP_N, al0, OP_N, ONE, NOMAT, ZERO, b, NU, mask));          // P = K^{-1} al
-        CU(eng.gemm(T[5], be0, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, mask));             // Q = be g
-        CU(eng.gemm(T[6], T[3], OP_N, T[2], OP_N, MONE, NOMAT, ZERO, b, NU, mask));        // S = -K^{-1} F
+        if ((sc = compact(mask, cnt)) != NEGF_OK) return sc;
+        CU(lgemm(T[4], T[3], OP_N, al0, OP_N, ONE, NOMAT, ZERO, mask));          // P = K^{-1} al
+        CU(lgemm(T[5], be0, OP_N, g, OP_N, ONE, NOMAT, ZERO, mask));             // Q = be g
+        CU(lgemm(T[6], T[3], OP_N, T[2], OP_N, MONE, NOMAT, ZERO, mask));        // S = -K^{-1} F
         CU(cudaMemcpyAsync(act, mask, sizeof(int) * NU, cudaMemcpyDeviceToDevice, s));
         BMat Pm = T[4], Qm = T[5], Sm = T[6], W1 = T[0], W2 = T[2], W3 = T[3];
         for (int j = 0; j < 96; ++j) {
-          CU(eng.gemm(W1, Pm, OP_N, Sm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P S
-          CU(eng.gemm(W2, W1, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P S Q
+          CU(lgemm(W1, Pm, OP_N, Sm, OP_N, ONE, NOMAT, ZERO, act));              // P S
+          CU(lgemm(W2, W1, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, act));              // P S Q
           smith_accum_kernel<<<NU, 256, 0, s>>>(Sm, W2, b, act, 1e-15);
           KCHECK();
-          CU(eng.gemm(W1, Pm, OP_N, Pm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // P^2
-          CU(eng.gemm(W3, Qm, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // Q^2
+          CU(lgemm(W1, Pm, OP_N, Pm, OP_N, ONE, NOMAT, ZERO, act));              // P^2
+          CU(lgemm(W3, Qm, OP_N, Qm, OP_N, ONE, NOMAT, ZERO, act));              // Q^2
           std::swap(Pm, W1);
           std::swap(Qm, W3);
           balance_kernel<<<NU, 256, 0, s>>>(Pm, Qm, b, act);
           KCHECK();
           if ((j & 7) == 7) {
-            const int cnt = n_set(act);
-            if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
-            if (cnt == 0) break;
+            const int c2 = n_set(act);
+            if (c2 < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
+            if (c2 == 0) break;
+            if ((sc = compact(act, c2)) != NEGF_OK) return sc;
           }
         }
+        ncomp = 0;
         add_kernel<<<eg, 256, 0, s>>>(gn, g, Sm, b, mask);                                  // g + D
         KCHECK();
         return residual(gn, resn, mask);
@@ -2479,7 +2543,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
           const int cnt = n_set(need);
           if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
           if (cnt == 0) break;
-          if ((st = newton_step(need, eps)) != NEGF_OK) return st;   // eps is free until the decimation
+          if ((st = newton_step(need, eps, cnt)) != NEGF_OK) return st;   // eps is free until the decimation
           newton_take_kernel<<<NU, 256, 0, s>>>(g, eps, b, res, resn, need, target, nsteps);
           KCHECK();
         }
@@ -2498,7 +2562,8 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
       if (n_cold > 0) {
         // ---- decimation
         for (int it = 0; it <= max_iter; ++it) {
-          const bool poll = (it & 3) == 3 || it == max_iter;
+          // counts after the first step (most units end there) and every fourth
+          const bool poll = it == 1 || (it & 3) == 3 || it == max_iter;
           if (poll) CU(cudaMemsetAsync(n_active, 0, sizeof(int), s));
           lead_norm_kernel<<<NU, 256, 0, s>>>(al, be, b, 1, ref, done, act, it_arr, it, tol,
                                               poll ? n_active : nullptr);
@@ -2507,20 +2572,22 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
             CU(cudaMemcpyAsync(ctx->h_pinned, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             if (ctx->h_pinned[0] == 0) break;
+            if ((st = compact(act, ctx->h_pinned[0])) != NEGF_OK) return st;
           }
           if (it == max_iter) break;
           if ((st = lead_inverse(g, eps, act)) != NEGF_OK) return st;        // g = eps^{-1}
-          CU(eng.gemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // al g
-          CU(eng.gemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, b, NU, act));              // be g
-          CU(eng.gemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // al g be
-          CU(eng.gemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, b, NU, act));           // be g al
+          CU(lgemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, act));              // al g
+          CU(lgemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, act));              // be g
+          CU(lgemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, act));           // al g be
+          CU(lgemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, act));           // be g al
           lead_update_kernel<<<eg, 256, 0, s>>>(eps, epss, T[2], T[3], b, done);
           KCHECK();
-          CU(eng.gemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -al g al
-          CU(eng.gemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, b, NU, act));          // -be g be
+          CU(lgemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, act));          // -al g al
+          CU(lgemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, act));          // -be g be
           std::swap(al, T[4]);
           std::swap(be, T[5]);
         }
+        ncomp = 0;
         // ---- surface function and its residual
         if ((st = lead_inverse(g, epss, any_warm ? cold : nullptr)) != NEGF_OK) return st;
         if ((st = residual(g, res, any_warm ? cold : nullptr)) != NEGF_OK) return st;
@@ -2532,7 +2599,7 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
           const int cnt = n_set(need);
           if (cnt < 0) return fail(ctx, NEGF_ERR_CUDA, "OBC: flag read-back failed");
           if (cnt == 0) break;
-          if ((st = newton_step(need, gn)) != NEGF_OK) return st;
+          if ((st = newton_step(need, gn, cnt)) != NEGF_OK) return st;
           newton_accept_kernel<<<NU, 256, 0, s>>>(g, gn, b, res, resn, need, target, nsteps);
           KCHECK();
           // units that took the step continue from T1/T2 (K, F of the accepted g)
