@@ -321,6 +321,14 @@ def rel_block_err(a, b, nblk):
     return float((num / den).max())
 
 
+def current_error(J_mixed, J_ref, grid_max):
+    """The scalar reading of the current's error: max over the sampled energies and
+    interfaces of |J_mixed - J_ref| / max(|J_ref|, 1e-3 grid_max), with grid_max the
+    largest |J| over the whole energy grid."""
+    floor = 1e-3 * max(float(grid_max), 1e-300)
+    return float((np.abs(J_mixed - J_ref) / np.maximum(np.abs(J_ref), floor)).max())
+
+
 def observables_vs_fp64(P, ctx, s2, o2, out, idx, w, ne, nb, b):
     """Mixed-vs-FP64 error of the current and the density on the sampled energies.
     The mixed blocks of those energies are gathered into a copy of the FP64 run's
@@ -344,8 +352,7 @@ def observables_vs_fp64(P, ctx, s2, o2, out, idx, w, ne, nb, b):
     J64, Jm = o2["current"].cpu().numpy(), o3["current"].cpu().numpy()
     n64, nm = o2["density"].cpu().numpy(), o3["density"].cpu().numpy()
     J_grid_max = float(out["current"].abs().max().item())
-    floor = 1e-3 * max(J_grid_max, 1e-300)
-    res["J"] = float((np.abs(Jm - J64) / np.maximum(np.abs(J64), floor)).max())
+    res["J"] = current_error(Jm, J64, J_grid_max)
     res["n"] = float(np.linalg.norm(nm - n64) / max(np.linalg.norm(n64), 1e-300))
     res["J_max_abs"] = float(np.abs(J64).max())
     res["J_grid_max_abs"] = J_grid_max
@@ -710,13 +717,13 @@ def run_config4(args):
     torch.cuda.synchronize()
     J64 = o2["current"].cpu().numpy().reshape(k, dev.nb - 1)
     Jm = J.cpu().numpy().reshape(dev.ne, dev.nb - 1)[idx]
-    floor = 1e-3 * max(float(np.abs(J.cpu().numpy()).max()), 1e-300)   # max_E over all energies (mixed)
+    J_grid_max = float(np.abs(J.cpu().numpy()).max())   # max_E over all energies (mixed)
     line = {"workload": "config4", "devices": 1, "energies": dev.ne, "nb": dev.nb, "b": dev.b,
             "mixed": {"value": dev.ne / ((ms_obc + ms_sw) / 1e3), "unit": UNIT, "ms_per_run": ms_obc + ms_sw,
                       "ms_obc": ms_obc, "ms_sweeps_and_observables": ms_sw,
                       "what": "OBC + G^R/G^< sweeps + T, DOS, current, density over all 512 energies, mixed "
                               "precision, blocks kept in the workspace chunk by chunk (negf_rgf_observables)"},
-            "J_err_vs_fp64": float((np.abs(Jm - J64) / np.maximum(np.abs(J64), floor)).max()),
+            "J_err_vs_fp64": current_error(Jm, J64, J_grid_max),
             "fp64_sampled_energies": idx.tolist(),
             "finite": bool(np.isfinite(J.cpu().numpy()).all() and np.isfinite(n.cpu().numpy()).all()),
             "status": {"obc_not_converged": int((st_obc != 0).sum().item()),

@@ -173,3 +173,16 @@ def test_rank_weights_one_rank_is_the_local_trapezoid():
     assert np.array_equal(bench.rank_weights(64, 0, 1), bench.W.trapezoid_weights(np.linspace(-3.0, 3.0, 64)))
     parts = [bench.rank_weights(8, r, 4) for r in range(4)]
     assert abs(sum(p.sum() for p in parts) - 6.0) < 1e-12
+
+
+def test_current_error_floor_comes_from_the_whole_grid():
+    """The scalar reading |dJ| / max(|J|, 1e-3 max_E |J|) with max_E over the whole
+    energy grid: a tiny current far below the grid's peak is measured against the floor,
+    an energy above the floor against its own value."""
+    J_ref = np.array([[1e-9, 2e-9], [5e-4, 5e-4]])
+    J_mix = J_ref + np.array([[1e-12, -1e-12], [5e-10, 0.0]])
+    # grid peak 3e-3: floor 3e-6, so the tiny entries count 1e-12 / 3e-6
+    assert abs(bench.current_error(J_mix, J_ref, 3e-3) - 1e-6) < 1e-15
+    # a floor from the sample alone (peak 5e-4 -> 5e-7) would count them 2e-6
+    assert abs(bench.current_error(J_mix, J_ref, 5e-4) - 2e-6) < 1e-15
+    assert bench.current_error(J_ref, J_ref, 3e-3) == 0.0
