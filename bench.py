@@ -215,9 +215,9 @@ def roofline_for(cls, stats, peaks, peak_src, sustained=True):
     return out
 
 
-def traffic_for(cls):
-    """Per-launch DRAM traffic of the kernel class from the committed ncu summary,
-    or None when that capture does not match the current kernel source."""
+def traffic_record(cls):
+    """The committed ncu record of the kernel class (bytes and duration of one full
+    launch), or None when that capture does not match the current kernel source."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
@@ -233,7 +233,25 @@ def traffic_for(cls):
         h = hashlib.sha256(f.read()).hexdigest()[:16]
     if h != ent.get("source_sha256_16"):
         return None
-    return ent.get("bytes_per_launch_full")
+    return ent
+
+
+def traffic_for(cls):
+    """Per-launch DRAM traffic of the kernel class from the committed ncu summary,
+    or None when that capture does not match the current kernel source."""
+    ent = traffic_record(cls)
+    return ent.get("bytes_per_launch_full") if ent else None
+
+
+def hbm_for(cls, peaks, peak_src):
+    """Achieved DRAM bandwidth of one full launch of the kernel class (the ncu record's
+    bytes over its durations) against the HBM peak, or None without a current record."""
+    ent = traffic_record(cls)
+    if not ent or not ent.get("ms_per_launch_full"):
+        return None
+    gbs = ent["bytes_per_launch_full"] / (ent["ms_per_launch_full"] / 1e3) / 1e9
+    return {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+            "note": f"ncu DRAM bytes / duration of one full launch vs HBM copy peak ({peak_src})"}
 
 
 # ---------------------------------------------------------------------------
@@ -540,6 +558,7 @@ def run_gpu(args):
     dominant = max(cls_ms, key=cls_ms.get)
     roof = roofline_for(dominant, prof["classes"][dominant], peaks, src, sustained=True)
     roof["traffic"] = traffic_for(dominant)
+    roof["hbm"] = hbm_for(dominant, peaks, src)
     shares = {k: v / sum(cls_ms.values()) for k, v in cls_ms.items()}
 
     clocks = clk.summary()
@@ -732,6 +751,57 @@ def run_config4(args):
     ctx.close()
 
 
+def run_config1(args):
+    """Config 1, the small latency-bound case (nb 16, b 8, 64 energies): microseconds per
+    batch of all 64 energies for OBC + G^R/G^< sweeps + observables, per precision (b = 8
+    is below the sliced product's smallest block, so NEGF_MIXED takes the FP64 products
+    here and differs from NEGF_FP64 only in its FP32 inverses with refinement), and the
+    largest normwise G^R difference between the two precisions (the parity tests compare
+    config 1 with the CPU oracle).  Not a bench line."""
+    import torch
+    import paper_2602_03438_gb300 as P
+    torch.cuda.set_device(0)
+    dev = W.config1()
+    ctx = P.Context(0, 256 << 20)
+    sys_ = P.upload(dev)
+    out = P.allocate_outputs(sys_)
+    fL = torch.from_numpy(dev.f_L()).cuda()
+    fR = torch.from_numpy(dev.f_R()).cuda()
+    w = torch.from_numpy(dev.weights()).cuda()
+    res = {}
+    GR64 = None
+    for name, prec in (("fp64", P.FP64), ("mixed", P.MIXED)):
+        def step():
+            P.negf_obc(ctx, sys_, out["sigma_L"], out["sigma_R"], out["iters"], out["obc_status"], prec=prec)
+            P.negf_rgf_lesser(ctx, sys_, prec, out["sigma_L"], out["sigma_R"], fL, fR, None, out["GR_diag"],
+                              out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
+            P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
+                               out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"],
+                               out["density"], prec=prec)
+        for _ in range(max(args.warmup, 1)):
+            step()
+        if ctx.sync() != 0:
+            raise RuntimeError("device status after the warm-up")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(max(args.steps, 1)):
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e3)
+        GR = out["GR_diag"].cpu().numpy().reshape(dev.ne, -1)
+        res[name] = {"us_per_batch_median": float(np.median(times)), "us_per_batch_min": float(np.min(times))}
+        if GR64 is None:
+            GR64 = GR
+        else:
+            res[name]["GR_err_vs_fp64"] = float((np.linalg.norm(GR - GR64, axis=1) /
+                                                 np.linalg.norm(GR64, axis=1)).max())
+    print(json.dumps({"workload": "config1", "nb": dev.nb, "b": dev.b, "energies": dev.ne,
+                      "what": "OBC + G^R/G^< sweeps + T, DOS, current, density for all 64 energies, one batch",
+                      **res}), flush=True)
+
+
 def run_workload(args):
     """Mixed vs FP64 on the other workloads (not the headline line): --workload config4 runs
     the nb = 32, b = 512 device with block-diagonal scattering over `ne` energies;
@@ -875,7 +945,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe", choices=["gemm", "inverse", "partitioned"], default=None)
-    ap.add_argument("--workload", choices=["config3", "config4"], default=None)
+    ap.add_argument("--workload", choices=["config1", "config3", "config4"], default=None)
     ap.add_argument("--devices", type=int, default=16)
     ap.add_argument("--ne-cap", type=int, default=64)
     args = ap.parse_args(argv)
@@ -885,6 +955,8 @@ def main(argv=None):
         run_probe(args)
     elif args.workload == "config4":
         run_config4(args)
+    elif args.workload == "config1":
+        run_config1(args)
     elif args.workload:
         run_workload(args)
     elif args.impl == "reference":

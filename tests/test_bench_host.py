@@ -186,3 +186,13 @@ def test_current_error_floor_comes_from_the_whole_grid():
     # a floor from the sample alone (peak 5e-4 -> 5e-7) would count them 2e-6
     assert abs(bench.current_error(J_mix, J_ref, 5e-4) - 2e-6) < 1e-15
     assert bench.current_error(J_ref, J_ref, 3e-3) == 0.0
+
+
+def test_hbm_bandwidth_from_the_traffic_record():
+    rec = bench.traffic_record("gemm_oz")
+    if rec is None:
+        pytest.skip("the record does not match the current kernel source")
+    peaks = {"hbm_gbs": 6000.0}
+    h = bench.hbm_for("gemm_oz", peaks, "test")
+    gbs = rec["bytes_per_launch_full"] / (rec["ms_per_launch_full"] / 1e3) / 1e9
+    assert abs(h["achieved_gbs"] - gbs) < 1e-9 * gbs and abs(h["frac"] - gbs / 6000.0) < 1e-12
