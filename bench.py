@@ -797,6 +797,47 @@ def run_config1(args):
         else:
             res[name]["GR_err_vs_fp64"] = float((np.linalg.norm(GR - GR64, axis=1) /
                                                  np.linalg.norm(GR64, axis=1)).max())
+    # the sweeps and observables (mixed) as one CUDA graph captured on the caller's stream
+    # (they make no host synchronisation; the OBC polls the host between its steps and
+    # stays outside, its Sigma from the last run): the launch overhead of the small case
+    def sweeps_obs():
+        P.negf_rgf_lesser(ctx, sys_, P.MIXED, out["sigma_L"], out["sigma_R"], fL, fR, None, out["GR_diag"],
+                          out["GR_up"], out["GR_low"], out["GL_diag"], out["GL_low"], out["status"])
+        P.negf_observables(ctx, sys_, out["sigma_L"], w, out["GR_diag"], out["GR_up"], out["GR_low"],
+                           out["GL_diag"], out["GL_low"], out["T"], out["dos"], out["current"], out["density"],
+                           prec=P.MIXED)
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            sweeps_obs()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        direct = {k: out[k].clone() for k in ("GR_diag", "GL_diag", "current", "density")}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_direct = []
+        for _ in range(max(args.steps, 1)):
+            e0.record()
+            sweeps_obs()
+            e1.record()
+            torch.cuda.synchronize()
+            t_direct.append(e0.elapsed_time(e1) * 1e3)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            sweeps_obs()
+        t_graph = []
+        for _ in range(max(args.steps, 1)):
+            e0.record()
+            graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            t_graph.append(e0.elapsed_time(e1) * 1e3)
+        same = all(bool(torch.equal(direct[k], out[k])) for k in direct)
+        res["sweeps_and_observables_mixed"] = {"us_per_batch_direct": float(np.median(t_direct)),
+                                               "us_per_batch_graph": float(np.median(t_graph)),
+                                               "graph_replay_bit_identical": same}
+    except Exception as ex:   # a capture the runtime refuses is reported, not fatal
+        res["sweeps_and_observables_mixed"] = {"graph_error": str(ex)[:300]}
     print(json.dumps({"workload": "config1", "nb": dev.nb, "b": dev.b, "energies": dev.ne,
                       "what": "OBC + G^R/G^< sweeps + T, DOS, current, density for all 64 energies, one batch",
                       **res}), flush=True)
