@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libnegf.so")
-SOURCES = ["blas_batched.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_oz_lo.cu", "negf_api.cu", "noalloc.cu", "mlp.cu", "scba.cu"]
+SOURCES = ["blas_batched.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_oz_lo.cu", "negf_api.cu", "noalloc.cu", "mlp.cu", "scba.cu",
+           "rgf_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

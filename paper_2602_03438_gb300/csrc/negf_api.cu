@@ -193,6 +193,10 @@ struct AsmArgs {
   // A_ii = E S_ii + Wd_i, A_{j,j+1} = E S_up_j + Wu_j, A_{j+1,j} = (E S_up_j + Wl_j)^H
   // with E real: two FP64 FMAs per element instead of the complex z S - H
   const zc *Wd = nullptr, *Wu = nullptr, *Wl = nullptr;
+  // every block index in one launch (grid z = block index k, uniform batches only):
+  // A_kk, Sigma^x_kk and A_{k,k+1}, A_{k+1,k} (k < nb-1) into the slot arrays above,
+  // block stride units*b*b (i_diag, i_off unused)
+  int all_blocks = 0;
 };
 
 // Wd_i = -H_ii + i eta S_ii, Wu_j = -H_up_j + i eta S_up_j, Wl_j = -H_up_j - i eta S_up_j
@@ -247,6 +251,22 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
   }
   const int b = a.dv.b, nb = a.dv.nb;
   const long long bb = (long long)b * b;
+  if (a.all_blocks) {
+    const int k = blockIdx.z;
+    const long long sh = (long long)k * a.units * bb;
+    a.i_diag = k;
+    a.i_off = (k + 1 < nb) ? k : -1;
+    if (a.Adiag) a.Adiag += sh;
+    if (a.SigL) a.SigL += sh;
+    if (a.SigG) a.SigG += sh;
+    if (a.i_off < 0) {
+      a.Aup = nullptr;
+      a.Alow = nullptr;
+    } else {
+      if (a.Aup) a.Aup += sh;
+      if (a.Alow) a.Alow += sh;
+    }
+  }
   const int poff = (u % a.P) * a.L;
   const zc z = zmake(a.dv.E[e], a.dv.eta);
   const int ntile = (b + ASM_T - 1) / ASM_T;
@@ -370,10 +390,11 @@ __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a) {
 cudaError_t assemble(const AsmArgs& a, cudaStream_t s) {
   if (a.units <= 0) return cudaSuccess;
   const int nt = (a.dv.b + ASM_T - 1) / ASM_T;
+  const dim3 grid((unsigned)(nt * nt), a.units, a.all_blocks ? a.dv.nb : 1);
   if (a.Wd)
-    assemble_kernel<true><<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
+    assemble_kernel<true><<<grid, dim3(ASM_T, 8), 0, s>>>(a);
   else
-    assemble_kernel<false><<<dim3((unsigned)(nt * nt), a.units), dim3(ASM_T, 8), 0, s>>>(a);
+    assemble_kernel<false><<<grid, dim3(ASM_T, 8), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -615,12 +636,15 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   // ---- workspace slots (each U blocks, unit stride b*b)
   char* p = ws;
   auto slot = [&](int count) { zc* q = (zc*)p; p += blk * (size_t)U * count; return q; };
-  zc* Adiag = slot(1);
-  zc* Aup = slot(1);
-  zc* Alow = slot(1);
-  zc* SigL = io.lesser ? slot(1) : nullptr;
+  // small blocks: the whole sweep in one launch over blocks assembled for every index
+  const bool small = !bp && rgf_small_supported(b, eng.mixed);
+  const int nd = small ? nb : 1, no = small ? std::max(nb - 1, 1) : 1;
+  zc* Adiag = slot(nd);
+  zc* Aup = slot(no);
+  zc* Alow = slot(no);
+  zc* SigL = io.lesser ? slot(nd) : nullptr;
   const bool greater = io.lesser && io.greater;
-  zc* SigG = greater ? slot(1) : nullptr;
+  zc* SigG = greater ? slot(nd) : nullptr;
   zc* T[4];
   for (int k = 0; k < 4; ++k) T[k] = slot(1);
   zc* Ybase = slot(std::max(nb - 1, 1));
@@ -668,6 +692,45 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   }
   int32_t* st = bp ? bp->st_units : (io.status ? io.status + e0 : nullptr);
   const int* act = nullptr;   // this step's mask (uneven batch), else every unit
+
+  if (small) {
+    a.all_blocks = 1;
+    a.Adiag = Adiag; a.SigL = SigL; a.SigG = SigG;
+    a.Aup = nb > 1 ? Aup : nullptr;
+    a.Alow = nb > 1 ? Alow : nullptr;
+    ++ctx->launches;
+    CU(assemble(a, s));
+    const SBlk none{nullptr, 0, 0};
+    // an output array [e][i] from energy e0 on, else a workspace slot array [i][u]
+    auto diag = [&](zc* out, zc* w) {
+      return out ? SBlk{out + (long long)(e0 - eo) * nb * bb, (long long)nb * bb, bb} : SBlk{w, bb, (long long)U * bb};
+    };
+    auto offd = [&](zc* out) {
+      return out ? SBlk{out + (long long)(e0 - eo) * (nb - 1) * bb, (long long)(nb - 1) * bb, bb} : none;
+    };
+    SmallSweep w;
+    w.nb = nb; w.b = b; w.U = U; w.nk = (int)kinds.size();
+    w.Ad = Adiag; w.Au = Aup; w.Al = Alow; w.Sl = SigL; w.Sg = SigG;
+    w.Y = SBlk{Ybase, bb, (long long)U * bb};
+    w.gR = diag(io.GRd, gbase);
+    w.gL = io.lesser ? diag(io.GLd, glbase) : none;
+    w.gG = greater ? diag(io.GGd, ggbase) : none;
+    w.Ru = offd(io.GRu);
+    w.Rl = offd(io.GRl);
+    w.Ll = io.lesser ? offd(io.GLl) : none;
+    w.Gl = greater ? offd(io.GGl) : none;
+    w.status = st;
+    // useful work: nb inverses, the retarded products (2 per forward step, 3 or 4 per
+    // backward step) and per Keldysh kind 2 + 4 (nb - 1) forward and 4 or 5 per backward step
+    const int nk = w.nk, m = nb - 1;
+    const double prods = 2.0 * m + m * (3.0 + (io.GRl ? 1 : 0)) +
+                         nk * (2.0 + 4.0 * m + m * (4.0 + (io.GLl ? 1 : 0)));
+    const double blocks = nb * (5.0 + 2 * nk) + m * (5.0 + (io.GRu ? 1 : 0) + (io.GRl ? 1 : 0) + nk * 3.0);
+    eng.begin(K_GEMM_F64);
+    CU(rgf_small_sweep(w, s));
+    eng.end(8.0 * bb * b * (prods + nb) * U, 16.0 * bb * blocks * U);
+    return NEGF_OK;
+  }
 
   // ---------------- forward sweep
   for (int i = 0; i < nb; ++i) {
@@ -1081,6 +1144,8 @@ size_t rgf_bytes_per_energy(int nb, int b, const RgfIO& io, int mixed) {
   const size_t blk = sizeof(zc) * (size_t)b * b;
   const bool greater = io.lesser && io.greater;
   size_t n = 3 + (io.lesser ? 1 : 0) + (greater ? 1 : 0) + 4 + std::max(nb - 1, 1);
+  if (rgf_small_supported(b, mixed))   // blocks assembled for every index (one launch)
+    n += (size_t)(nb - 1) * (1 + (io.lesser ? 1 : 0) + (greater ? 1 : 0)) + 2 * (size_t)(std::max(nb - 1, 1) - 1);
   if (!io.GRd) n += nb;
   if (io.lesser && !io.GLd) n += nb;
   if (greater && !io.GGd) n += nb;

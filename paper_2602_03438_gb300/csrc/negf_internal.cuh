@@ -20,6 +20,7 @@ namespace negf {
 // is not recorded, so the next call retries it.
 // ---------------------------------------------------------------------------
 enum InitSlot { INIT_OZ = 0, INIT_OZS, INIT_OZP, INIT_OZT, INIT_TC, INIT_MLP, INIT_OZS_LO, INIT_OZP_LO, INIT_OZT_LO,
+                INIT_SMALL,
                 INIT_NSLOT };
 constexpr int kMaxDevices = 64;
 cudaError_t once_per_device(int slot, const std::function<cudaError_t(int device)>& init);
@@ -161,6 +162,30 @@ cudaError_t zgemm_ozt_variant(const GemmArgs& g, void* scratch, int* err, cudaSt
 cudaError_t zinv(BMat X, BMat M, int n, int units, const int* active, int single, void* scratch,
                  int32_t* status, cudaStream_t s);
 size_t zinv_scratch_bytes(int n, int units, int single);
+
+// block i of unit u at p + u us + i is (a device's diagonal or off-diagonal output
+// blocks, or a workspace slot array [i][u])
+struct SBlk {
+  zc* p;
+  long long us, is;
+  __host__ __device__ zc* at(int u, int i) const { return p + (long long)u * us + (long long)i * is; }
+};
+// the whole forward and backward sweep of U energies of one device with blocks of b <= 16
+// in one launch (one CTA per energy, FP64).  Ad [nb], Au/Al [nb-1], Sl/Sg [nb] hold the
+// assembled blocks with unit stride b*b and block stride U*b*b; Y: the workspace of the
+// products A_{i+1,i} g_i; gR, gL, gG: the diagonal blocks (left-connected on the forward
+// sweep, overwritten with G, G^<, G^> on the backward sweep); Ru, Rl, Ll, Gl: the
+// off-diagonal outputs G_{i,i+1}, G_{i+1,i}, G^<_{i+1,i}, G^>_{i+1,i} (p nullable);
+// nk Keldysh kinds (0: retarded only, 1: G^<, 2: G^< and G^>).  status[u] (nullable) gets
+// NEGF_ERR_SINGULAR on a zero pivot.
+struct SmallSweep {
+  int nb, b, U, nk;
+  const zc *Ad, *Au, *Al, *Sl, *Sg;
+  SBlk Y, gR, gL, gG, Ru, Rl, Ll, Gl;
+  int32_t* status;
+};
+bool rgf_small_supported(int b, int mixed);
+cudaError_t rgf_small_sweep(const SmallSweep& a, cudaStream_t s);
 
 // Eq. (3) on a uniform grid: Y[e][i] = sum_{m=-M..M} w_m X[e-m][i] for i < nelem (element i
 // of energy e at X + e ld + i), by a zero-padded FFT of size N = 2^conv_log2_size(ne, M)

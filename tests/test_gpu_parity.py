@@ -193,6 +193,31 @@ def test_uneven_batch_matches_single_devices(P, ctx):
             _check_energy(r, e, ref, TOL_FP64)
 
 
+
+@pytest.mark.parametrize("b", [3, 8, 16])
+def test_small_block_sweep_matches_batched_steps(P, ctx, b):
+    """Blocks of b <= 16 (FP64) run the whole sweep as one launch, one CTA per energy; the
+    same devices batched with another device of their block size run one launch per
+    sweep step over a work list.  With scattering, the two agree to rounding and each
+    matches the oracle."""
+    devs = [strong_leads(W.small_scattering_device(nb, b, ne, seed=700 + 10 * b + k, overlap=True,
+                                                   strength=0.05), seed=k)
+            for k, (nb, ne) in enumerate([(4, 5), (7, 3)])]
+    batched = run_gpu(P, ctx, devs, P.FP64)
+    for dev, rb in zip(devs, batched):
+        one = run_gpu(P, ctx, dev, P.FP64)[0]
+        assert np.all(one["status"] == 0) and np.all(rb["status"] == 0)
+        for k in GR_KEYS + GL_KEYS:
+            scale = np.abs(rb[k]).max()
+            assert np.abs(one[k] - rb[k]).max() <= 1e-11 * scale, k
+        for e in range(dev.ne):
+            ref = O.solve_energy(dev, e, sigma=(one["sigma_L"][e], one["sigma_R"][e]))
+            _check_energy(one, e, ref, TOL_FP64)
+        jscale = np.abs(rb["current"]).max()
+        assert np.abs(one["current"] - rb["current"]).max() <= 1e-10 * jscale
+        assert np.abs(one["density"] - rb["density"]).max() <= 1e-10 * np.abs(rb["density"]).max()
+
+
 # --- numerical status codes ---------------------------------------------------------
 
 def test_singular_block_flags_energy(P, ctx):
