@@ -278,8 +278,313 @@ __global__ void __launch_bounds__(kInvThreads) zinv_kernel(BMat X, BMat M, int n
   if (tid == 0 && s_sing && status) status[u] = NEGF_ERR_SINGULAR;
 }
 
+// ---------------------------------------------------------------------------
+// The same Gauss-Jordan inversion in panels of kPW columns.  The panel's pivot steps are
+// first applied to the panel's own columns only (pivot search, row interchange, scaling
+// and elimination exactly as above), recording the multiplier f_r of every row at each
+// step in F (F[k][j] = d_j on the pivot row).  The other columns then take the panel's
+// steps in one pass: with a column's rows permuted by the panel's interchanges into y,
+// the pivot rows' new values are v_j = (y_{k0+j} - sum_{j'<j} F[k0+j][j'] v_j') / d_j,
+// and row r becomes y_r - sum_j F[r][j] v_j, except pivot row k0+j, which becomes
+// v_j - sum_{j'>j} F[k0+j][j'] v_j'.  The same pivots and arithmetic up to rounding
+// order, with one pass over the matrix per panel instead of one per pivot step.
+// ---------------------------------------------------------------------------
+constexpr int kPW = 8;
+constexpr int kPanelThreads = 128;   // the panel's rows, one per thread (n <= 128)
+
+// a barrier of the first kPanelThreads threads only (the rest of the CTA waits at the
+// next full barrier)
+__device__ __forceinline__ void panel_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kPanelThreads) : "memory"); }
+
+template <typename R>
+static size_t panel_smem_bytes(int n) {
+  typedef typename CT<R>::T C;
+  return sizeof(C) * ((size_t)n * (n + 1) + 4 * (size_t)kPW * n) + 3 * sizeof(int) * (size_t)n + 16;
+}
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T cmul(typename CT<R>::T a, typename CT<R>::T b) {
+  return cmk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// the kPW multipliers of one row (16-byte loads: the row starts on a 16-byte boundary)
+template <typename R>
+__device__ __forceinline__ void load_row(typename CT<R>::T* f, const typename CT<R>::T* src) {
+  if (sizeof(typename CT<R>::T) == 8) {
+    const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int j = 0; j < kPW / 2; ++j) {
+      const float4 t = q[j];
+      f[2 * j].x = (R)t.x; f[2 * j].y = (R)t.y;
+      f[2 * j + 1].x = (R)t.z; f[2 * j + 1].y = (R)t.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kPW; ++j) f[j] = src[j];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) zinv_panel_kernel(BMat X, BMat M, int n, const int* active,
+                                                                 int32_t* status) {
+  typedef typename CT<R>::T C;
+  const int u = blockIdx.x;
+  if (active && !active[u]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = n + 1;
+  C* W = reinterpret_cast<C*>(smem_raw);   // n x ld
+  C* F = W + (size_t)n * ld;               // [row][kPW]: multipliers of the panel's steps
+  C* V = F + (size_t)n * kPW;              // [kPW][n]: new pivot-row values of the other columns
+  C* Stg = V + (size_t)kPW * n;            // [2 kPW][n]: rows moved by the panel's interchanges
+  int* piv = reinterpret_cast<int*>(Stg + (size_t)2 * kPW * n);
+  int* rowsrc = piv + n;                   // position -> row of W it holds after the interchanges
+  int* stage_of = rowsrc + n;              // position -> its slot in Stg, or -1
+  __shared__ C s_dinv[kPW];
+  __shared__ C s_prow[kPW];
+  __shared__ R s_cbest[kPanelThreads / 32];
+  __shared__ int s_cpos[kPanelThreads / 32];
+  __shared__ int s_sing;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const zc* Min = M.at(u);
+  const int nn = n * n;
+  for (int i = tid; i < nn; i += kInvThreads) {
+    const int r = i / n, c = i - r * n;
+    const zc v = Min[i];
+    W[(size_t)r * ld + c] = cmk<R>((R)v.x, (R)v.y);
+  }
+  for (int i = tid; i < n; i += kInvThreads) {
+    rowsrc[i] = i;
+    stage_of[i] = -1;
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+  const C zero = cmk<R>((R)0, (R)0);
+  const int rs = kInvThreads / n;          // >= kPW: n <= kInvThreads / kPW
+  const int mc = tid % n, r0 = tid / n;    // the other columns' pass: column and first row
+
+  for (int k0 = 0; k0 < n; k0 += kPW) {
+    const int w = min(kPW, n - k0);
+    // ---- the panel's pivot steps on its own columns, by the first kPanelThreads threads:
+    //      thread r keeps row r of the panel and its multipliers in registers, and the
+    //      interchanges move positions (mypos: where row r stands) instead of data; two
+    //      barriers of these warps per step
+    if (tid < kPanelThreads) {
+      const int r = tid;
+      const bool has = r < n;
+      C pw[kPW];
+      C* pf = Stg + r * kPW;   // row r's multipliers (the staging buffer is free until the panel ends)
+      int mypos = r;
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) pw[j] = (has && j < w) ? W[r * ld + k0 + j] : zero;
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        if (j < w) {
+          const int k = k0 + j;
+          // pivot: the smallest position >= k holding the largest |.|^2 of column j
+          R best = (R)-1;
+          int bp = n;
+          if (has && mypos >= k) {
+            best = pw[j].x * pw[j].x + pw[j].y * pw[j].y;
+            bp = mypos;
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const R ob = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bp, off);
+            if (ob > best || (ob == best && oi < bp)) { best = ob; bp = oi; }
+          }
+          if (lane == 0) {
+            s_cbest[tid >> 5] = best;
+            s_cpos[tid >> 5] = bp;
+          }
+          panel_barrier();
+          best = s_cbest[0];
+          int p = s_cpos[0];
+#pragma unroll
+          for (int q = 1; q < kPanelThreads / 32; ++q) {
+            const R ob = s_cbest[q];
+            const int oi = s_cpos[q];
+            if (ob > best || (ob == best && oi < p)) { best = ob; p = oi; }
+          }
+          if (!(best > (R)0)) p = k;   // singular: the row at position k stays
+          const bool win = has && mypos == p;
+          if (win) {
+            const C d = pw[j];
+            const R den = d.x * d.x + d.y * d.y;
+            const C dinv = (den > (R)0) ? cmk<R>(d.x / den, -d.y / den) : zero;
+#pragma unroll
+            for (int c = 0; c < kPW; ++c) s_prow[c] = (c == j) ? dinv : cmul<R>(pw[c], dinv);
+            s_dinv[j] = dinv;
+            piv[k] = p;
+            if (!(best > (R)0)) s_sing = 1;
+          }
+          panel_barrier();
+          if (has) {
+            if (win) {
+              pf[j] = pw[j];   // F[k][j] = d
+#pragma unroll
+              for (int c = 0; c < kPW; ++c) pw[c] = s_prow[c];
+            } else {
+              const C f = pw[j];
+              pf[j] = f;
+#pragma unroll
+              for (int c = 0; c < kPW; ++c) {
+                const C pc = s_prow[c];
+                if (c == j) {
+                  pw[c] = cmk<R>(-(f.x * pc.x - f.y * pc.y), -(f.x * pc.y + f.y * pc.x));
+                } else {
+                  pw[c].x -= f.x * pc.x - f.y * pc.y;
+                  pw[c].y -= f.x * pc.y + f.y * pc.x;
+                }
+              }
+            }
+            if (mypos == k) mypos = p;   // the row at position k takes the pivot row's place
+            if (win) mypos = k;
+          }
+        }
+      }
+      // the panel's columns and multipliers at the rows' final positions
+      if (has) {
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          if (j < w) {
+            W[mypos * ld + k0 + j] = pw[j];
+            F[mypos * kPW + j] = pf[j];   // this thread's own entries
+          }
+        }
+        rowsrc[mypos] = r;
+      }
+    }
+    __syncthreads();
+    // ---- stage the rows that the interchanges moved (positions k0 .. k0+w-1 and the
+    //      pivot rows' old positions; a position listed twice holds the same row in both
+    //      slots) and the other columns' new pivot-row values
+    if (tid < 2 * w) stage_of[tid < w ? k0 + tid : piv[k0 + tid - w]] = tid;
+    for (int i = tid; i < 2 * w * n; i += kInvThreads) {
+      const int sl = i / n, c = i - sl * n;
+      const int pos = sl < w ? k0 + sl : piv[k0 + sl - w];
+      Stg[(size_t)sl * n + c] = W[(size_t)rowsrc[pos] * ld + c];
+    }
+    if (tid < n && (tid < k0 || tid >= k0 + w)) {
+      C v[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        if (j < w) {
+          C a = W[(size_t)rowsrc[k0 + j] * ld + tid];
+#pragma unroll
+          for (int q = 0; q < kPW; ++q) {
+            if (q < j) {
+              const C f = F[(size_t)(k0 + j) * kPW + q];
+              a.x -= f.x * v[q].x - f.y * v[q].y;
+              a.y -= f.x * v[q].y + f.y * v[q].x;
+            }
+          }
+          v[j] = cmul<R>(a, s_dinv[j]);
+          V[(size_t)j * n + tid] = v[j];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- the other columns take the panel's steps in one pass
+    if (r0 < rs && (mc < k0 || mc >= k0 + w) && w == kPW) {
+      // a full panel: the rows other than the pivot rows with no per-step guards (a warp
+      // shares its row, so the pivot-row and moved-row branches are uniform), then this
+      // thread's pivot rows
+      C v[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) v[j] = V[j * n + mc];
+      C* wp = W + r0 * ld + mc;
+      const C* fp = F + r0 * kPW;
+      for (int r = r0; r < n; r += rs, wp += rs * ld, fp += rs * kPW) {
+        if (r >= k0 && r < k0 + kPW) continue;
+        const int sl = stage_of[r];
+        C a = (sl >= 0) ? Stg[sl * n + mc] : *wp;
+        C f[kPW];
+        load_row<R>(f, fp);
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          a.x -= f[j].x * v[j].x - f[j].y * v[j].y;
+          a.y -= f[j].x * v[j].y + f[j].y * v[j].x;
+        }
+        *wp = a;
+      }
+      for (int r = k0 + ((r0 - k0) % rs + rs) % rs; r < k0 + kPW; r += rs) {
+        const int jr = r - k0;
+        C f[kPW];
+        load_row<R>(f, F + r * kPW);
+        C a = zero;
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          if (j == jr) a = v[j];
+          if (j > jr) {
+            a.x -= f[j].x * v[j].x - f[j].y * v[j].y;
+            a.y -= f[j].x * v[j].y + f[j].y * v[j].x;
+          }
+        }
+        W[r * ld + mc] = a;
+      }
+    } else if (r0 < rs && (mc < k0 || mc >= k0 + w)) {
+      C v[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) v[j] = (j < w) ? V[(size_t)j * n + mc] : zero;
+      for (int r = r0; r < n; r += rs) {
+        const bool pivot_row = r >= k0 && r < k0 + w;
+        const int jr = r - k0;
+        C a;
+        if (pivot_row) {
+          a = zero;
+#pragma unroll
+          for (int j = 0; j < kPW; ++j)
+            if (j == jr) a = v[j];
+        } else {
+          const int sl = stage_of[r];
+          a = (sl >= 0) ? Stg[(size_t)sl * n + mc] : W[(size_t)r * ld + mc];
+        }
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          if (j < w && (!pivot_row || j > jr)) {
+            const C f = F[(size_t)r * kPW + j];
+            a.x -= f.x * v[j].x - f.y * v[j].y;
+            a.y -= f.x * v[j].y + f.y * v[j].x;
+          }
+        }
+        W[(size_t)r * ld + mc] = a;
+      }
+    }
+    __syncthreads();
+    // the matrix is in the panel's row order now: the next panel starts from the identity
+    // map (only the moved positions differ from it)
+    if (tid < 2 * w) {
+      const int pos = tid < w ? k0 + tid : piv[k0 + tid - w];
+      stage_of[pos] = -1;
+      rowsrc[pos] = pos;
+    }
+    // (the next panel's first barrier orders this before its staging)
+  }
+  // -- undo the row interchanges: swap columns k and piv[k], last pivot first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k) {
+      for (int r = tid; r < n; r += kInvThreads) {
+        C t = W[(size_t)r * ld + k];
+        W[(size_t)r * ld + k] = W[(size_t)r * ld + p];
+        W[(size_t)r * ld + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+  zc* Xo = X.at(u);
+  for (int i = tid; i < nn; i += kInvThreads) {
+    const int r = i / n, c = i - r * n;
+    const C v = W[(size_t)r * ld + c];
+    Xo[i] = zmake((double)v.x, (double)v.y);
+  }
+  if (tid == 0 && s_sing && status) status[u] = NEGF_ERR_SINGULAR;
+}
+
 static size_t inv_tail_bytes(int n, size_t csz) { return 3 * csz * n + sizeof(int) * n + 16; }
 static const size_t kInvSmemMax = 200 * 1024;
+static const size_t kPanelSmemMax = 227 * 1024;
 
 size_t zinv_scratch_bytes(int n, int units, int single) {
   const size_t csz = single ? sizeof(float2) : sizeof(double2);
@@ -292,7 +597,14 @@ static cudaError_t launch_inv(BMat X, BMat M, int n, int units, const int* activ
                               int32_t* status, cudaStream_t s) {
   typedef typename CT<R>::T C;
   const size_t full = sizeof(C) * (size_t)n * (n + 1) + inv_tail_bytes(n, sizeof(C));
-  if (full <= kInvSmemMax) {
+  const size_t pbytes = panel_smem_bytes<R>(n);
+  // panels for the FP32 inverse (the FP64 instance would spill its panel values)
+  if (sizeof(R) == 4 && n >= 16 && n <= kPanelThreads && pbytes <= kPanelSmemMax) {
+    cudaError_t e = cudaFuncSetAttribute(zinv_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pbytes);
+    if (e != cudaSuccess) return e;
+    zinv_panel_kernel<R><<<units, kInvThreads, pbytes, s>>>(X, M, n, active, status);
+  } else if (full <= kInvSmemMax) {
     cudaError_t e = cudaFuncSetAttribute(zinv_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)full);
     if (e != cudaSuccess) return e;

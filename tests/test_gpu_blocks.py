@@ -130,6 +130,42 @@ def test_block_inverse(P, ctx, n, prec):
         assert err <= tol, (u, err)
 
 
+@pytest.mark.parametrize("n", [16, 24, 70, 128])
+def test_block_inverse_with_interchanges(P, ctx, n):
+    """Dense complex normal matrices (no diagonal dominance): partial pivoting interchanges
+    rows at most steps, across the panels of the blocked FP32 Gauss-Jordan (8 columns per
+    panel; n = 70 ends on a panel of 6).  Mixed: the FP32 inverse refined twice."""
+    rng = np.random.default_rng(900 + n)
+    U = 4
+    M = _rand(rng, (U, n, n))
+    ref = np.linalg.inv(M)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    for prec, tol in (("MIXED", 1e-10), ("FP64", 1e-12)):
+        X = torch.empty((U, n, n), dtype=torch.complex128, device="cuda")
+        st = torch.zeros(U, dtype=torch.int32, device="cuda")
+        P.negf.negf_block_inverse(ctx, getattr(P, prec), t(M), X, st)
+        assert ctx.sync() == 0
+        assert st.cpu().numpy().tolist() == [0] * U
+        for u in range(U):
+            err = np.linalg.norm(X[u].cpu().numpy() - ref[u]) / np.linalg.norm(ref[u])
+            assert err <= tol, (prec, u, err)
+
+
+def test_block_inverse_singular_panels(P, ctx):
+    """A zero column found by the blocked FP32 Gauss-Jordan (n = 24, column 13, in the
+    second panel) flags its unit; the identity next to it does not."""
+    n = 24
+    rng = np.random.default_rng(7)
+    M = np.stack([_rand(rng, (n, n)), np.eye(n, dtype=complex)])
+    M[0, :, 13] = 0.0
+    X = torch.empty((2, n, n), dtype=torch.complex128, device="cuda")
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    P.negf.negf_block_inverse(ctx, P.MIXED, torch.from_numpy(M).cuda(), X, st)
+    assert ctx.sync() == 0
+    assert st.cpu().numpy().tolist() == [P.negf.NEGF_ERR_SINGULAR, 0]
+    assert np.abs(X[1].cpu().numpy() - np.eye(n)).max() <= 1e-14
+
+
 def test_block_inverse_singular(P, ctx):
     n = 6
     M = np.zeros((2, n, n), complex)
