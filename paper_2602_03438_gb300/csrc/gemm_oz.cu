@@ -1689,11 +1689,13 @@ static cudaError_t zgemm_ozs(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.eb = im.ea + (size_t)n * g.units;
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
-  // A digit images and op(B)'s column scales in one launch (n <= 96 here)
+  // A digit images and op(B)'s column scales in one launch (n <= 96 here); with reuse_a
+  // the one CTA per unit that makes op(B)'s scales
+  const dim3 pre((g.reuse_a ? 0 : (n + PRE_ROWS - 1) / PRE_ROWS) + 1, g.units);
   if (g.A.plain() && g.B.plain())
-    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(plain_args(g), im, 1);
+    oz_digitize_a2_kernel<<<pre, 256, 0, s>>>(plain_args(g), im, 1);
   else
-    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
+    oz_digitize_a2_kernel<<<pre, 256, 0, s>>>(g, im, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&
@@ -1768,11 +1770,13 @@ static cudaError_t zgemm_ozp(const GemmArgs& g, void* scratch, int* err, cudaStr
   im.eb = im.ea + (size_t)n * g.units;
   p += (sizeof(int) * 2 * (size_t)n * g.units + 1023) & ~(size_t)1023;
   im.a = p;
-  // A digit images and op(B)'s column scales in one launch
+  // A digit images and op(B)'s column scales in one launch; with reuse_a the one CTA per
+  // unit that makes op(B)'s scales
+  const dim3 pre((g.reuse_a ? 0 : (n + PRE_ROWS - 1) / PRE_ROWS) + 1, g.units);
   if (g.A.plain() && g.B.plain())
-    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(plain_args(g), im, 1);
+    oz_digitize_a2_kernel<<<pre, 256, 0, s>>>(plain_args(g), im, 1);
   else
-    oz_digitize_a2_kernel<<<dim3((n + PRE_ROWS - 1) / PRE_ROWS + 1, g.units), 256, 0, s>>>(g, im, 1);
+    oz_digitize_a2_kernel<<<pre, 256, 0, s>>>(g, im, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int unit_ab = ((g.alpha.y == 0.0 && (g.alpha.x == 1.0 || g.alpha.x == -1.0)) &&

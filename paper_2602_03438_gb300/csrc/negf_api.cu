@@ -454,10 +454,48 @@ struct Engine {
   bool can_slice(int n) const {
     return ozt_scratch ? oz_supported(n) : (oz_scratch != nullptr && oz_inkernel_supported(n));
   }
-  cudaError_t sliced(const GemmArgs& g) {
-    if (!ozt_scratch) return zgemm_oz(g, oz_scratch, ctx->d_err, s);
+  // op(A) of the last 8-digit digitize-once product whose scales and digit images are
+  // still in the scratch (n <= 128: the kernels whose images cover all of K); any other
+  // use of the scratch clears it
+  struct AKey {
+    const zc* p = nullptr;
+    long long us = 0, us2 = 0;
+    int inner = 0, opA = 0, n = 0, units = 0, variant = 0;
+    const long long* off = nullptr;
+    const int* active = nullptr;
+    const void* scratch = nullptr;
+    bool operator==(const AKey& o) const {
+      return p == o.p && us == o.us && us2 == o.us2 && inner == o.inner && opA == o.opA && n == o.n &&
+             units == o.units && variant == o.variant && off == o.off && active == o.active && scratch == o.scratch;
+    }
+  };
+  AKey last_a;   // p == nullptr: none
+  static AKey key_of(const GemmArgs& g, int variant, const void* scratch) {
+    AKey k;
+    k.p = g.A.p; k.us = g.A.us; k.us2 = g.A.us2; k.inner = g.A.inner; k.off = g.A.off;
+    k.opA = g.opA; k.n = g.n; k.units = g.units; k.active = g.active; k.variant = variant; k.scratch = scratch;
+    return k;
+  }
+  // `reuse`: the caller asks to reuse op(A)'s images when the last product left them
+  // (granted only when every field of the operand key matches)
+  cudaError_t sliced(GemmArgs g, bool reuse = false) {
+    if (!ozt_scratch) {
+      last_a = AKey();
+      return zgemm_oz(g, oz_scratch, ctx->d_err, s);
+    }
     const int v = (g.n >= 0 && g.n <= 512) ? ctx->oz_variant[g.n] : OZ_DEFAULT;
-    return zgemm_ozt_variant(g, ozt_scratch, ctx->d_err, s, v);
+    const int eff = (v == OZ_DEFAULT) ? (g.n <= 96 ? OZ_HALF : g.n <= 128 ? OZ_PERSISTENT : OZ_FULL) : v;
+    const AKey k = key_of(g, eff, ozt_scratch);
+    const bool keepable = eff != OZ_FULL && g.n <= 128;
+    g.reuse_a = (reuse && keepable && last_a.p && last_a == k) ? 1 : 0;
+    cudaError_t e = zgemm_ozt_variant(g, ozt_scratch, ctx->d_err, s, v);
+    // the images stay valid for the next product unless this one overwrote its own A
+    last_a = (e == cudaSuccess && keepable && g.D.p != g.A.p) ? k : AKey();
+    return e;
+  }
+  cudaError_t sliced_lo(const GemmArgs& g) {   // the 5-digit product: its own images in the scratch
+    last_a = AKey();
+    return zgemm_ozt_lo(g, ozt_scratch, ctx->d_err, s);
   }
   // timing facility: events around one launch of class `cls`
   int open_cls = -1;
@@ -479,8 +517,9 @@ struct Engine {
   // share of the units a masked launch works on, when the caller knows it (the batched
   // sweeps of an uneven batch); < 0: unknown (such launches are counted as "other")
   double active_frac = -1.0;
+  // reuse_a: op(A) is the previous product's op(A), unchanged since (see sliced)
   cudaError_t gemm(BMat D, BMat A, int opA, BMat B, int opB, zc alpha, BMat C, zc beta, int n, int units,
-                   const int* active = nullptr) {
+                   const int* active = nullptr, bool reuse_a = false) {
     GemmArgs g;
     g.D = D; g.A = A; g.B = B; g.C = C;
     g.opA = opA; g.opB = opB; g.alpha = alpha; g.beta = beta;
@@ -493,7 +532,7 @@ struct Engine {
     const bool masked = active != nullptr && active_frac < 0.0;   // an unknown share of the work
     if (mixed == 1 && can_slice(n)) {
       begin(masked ? K_OTHER : K_GEMM_OZ);
-      e = sliced(g);
+      e = sliced(g, reuse_a);
     } else if (mixed == 2 && tc_supported(n)) {
       begin(masked ? K_OTHER : K_GEMM_TC);
       e = zgemm_tc(g, ctx->d_err, s);
@@ -571,7 +610,7 @@ struct Engine {
         c.n = n; c.units = units; c.active = active;
         const bool masked = active != nullptr && active_frac < 0.0;
         begin(masked ? K_OTHER : (n <= 128 ? K_GEMM_OZ_LO : K_GEMM_OZ));
-        e = (n <= 128) ? zgemm_ozt_lo(c, ozt_scratch, ctx->d_err, s) : sliced(c);
+        e = (n <= 128) ? sliced_lo(c) : sliced(c);
         end(masked ? 0.0 : 8.0 * (double)n * n * n * units * frac, masked ? 0.0 : 64.0 * (double)n * n * units * frac);
         if (e != cudaSuccess) return e;
         continue;
@@ -750,16 +789,22 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
       }
       continue;
     }
-    // Y_{i-1} = A_{i,i-1} g_{i-1};  M = A_ii - Y_{i-1} A_{i-1,i};  g_i = M^{-1}
+    // Y_{i-1} = A_{i,i-1} g_{i-1};  M = A_ii - Y_{i-1} A_{i-1,i};  g_i = M^{-1}.  The first
+    // Keldysh kind's A_{i,i-1} g^x_{i-1} right after Y (the same left operand: the sliced
+    // product keeps its digit images), into T3, which the inverse leaves alone
     CU(eng.gemm(Yb(i - 1), S1(Alow), OP_N, gD(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act));
+    if (!kinds.empty())
+      CU(eng.gemm(S1(T[3]), S1(Alow), OP_N, kinds[0].D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act, true));
     CU(eng.gemm(S1(T[0]), Yb(i - 1), OP_N, S1(Aup), OP_N, MONE, S1(Adiag), ONE, b, U, act));
     CU(eng.inverse(gD(i), S1(T[0]), b, U, st, S1(T[1]), S1(T[2]), -1, act));
-    for (const Kind& k : kinds) {
+    for (size_t x = 0; x < kinds.size(); ++x) {
+      const Kind& k = kinds[x];
       // g^x_i = g_i (Sigma^x_ii + A_{i,i-1} g^x_{i-1} A_{i,i-1}^H) g_i^H   (x = <, >)
-      CU(eng.gemm(S1(T[1]), S1(Alow), OP_N, k.D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act));
-      CU(eng.gemm(S1(T[2]), S1(T[1]), OP_N, S1(Alow), OP_H, ONE, S1(k.sig), ONE, b, U, act));
-      CU(eng.gemm(S1(T[3]), gD(i), OP_N, S1(T[2]), OP_N, ONE, NOMAT, ZERO, b, U, act));
-      CU(eng.gemm(k.D(i), S1(T[3]), OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U, act));
+      const BMat T1 = S1(x == 0 ? T[3] : T[1]), T3 = S1(x == 0 ? T[1] : T[3]);
+      if (x > 0) CU(eng.gemm(T1, S1(Alow), OP_N, k.D(i - 1), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(S1(T[2]), T1, OP_N, S1(Alow), OP_H, ONE, S1(k.sig), ONE, b, U, act));
+      CU(eng.gemm(T3, gD(i), OP_N, S1(T[2]), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(k.D(i), T3, OP_N, gD(i), OP_H, ONE, NOMAT, ZERO, b, U, act));
     }
   }
   // ---------------- backward sweep
@@ -773,22 +818,38 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
     CU(assemble(a, s));
     const BMat X = S1(T[0]);
     const BMat Gup = io.GRu ? offB(io.GRu, i) : S1(gup_tmp);
-    // X = g_i A_{i,i+1};  G_{i,i+1} = -X G_{i+1,i+1};  G_ii = g_i - G_{i,i+1} Y_i;  G_{i+1,i} = -G_{i+1,i+1} Y_i
+    // X = g_i A_{i,i+1};  G_{i,i+1} = -X G_{i+1,i+1};  G_ii = g_i - G_{i,i+1} Y_i;  G_{i+1,i} = -G_{i+1,i+1} Y_i;
+    // per Keldysh kind x = <, >:  Z = A_{i+1,i} g^x_i,  P = G^x_{i+1,i+1} X^H,  W = G_{i,i+1} Z,
+    // G^x_ii = g^x_i + X P - W + W^H,  G^x_{i+1,i} = -G_{i+1,i+1} Z - P.
+    // The first kind's products are ordered so that the pairs with the same left operand
+    // (X; G_{i,i+1}; G_{i+1,i+1}) run back to back: the sliced product keeps that
+    // operand's digit images for the second of each pair
     CU(eng.gemm(X, gD(i), OP_N, S1(Aup), OP_N, ONE, NOMAT, ZERO, b, U, act));
+    const Kind* k0 = kinds.empty() ? nullptr : &kinds[0];
+    const BMat Z = S1(T[1]), P = S1(T[2]), Wm = S1(T[3]);
+    if (k0) {
+      CU(eng.gemm(Z, S1(Alow), OP_N, k0->D(i), OP_N, ONE, NOMAT, ZERO, b, U, act));
+      CU(eng.gemm(P, k0->D(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U, act));
+    }
     CU(eng.gemm(Gup, X, OP_N, gD(i + 1), OP_N, MONE, NOMAT, ZERO, b, U, act));
+    if (k0) CU(eng.gemm(k0->D(i), X, OP_N, P, OP_N, ONE, k0->D(i), ONE, b, U, act, true));
     CU(eng.gemm(gD(i), Gup, OP_N, Yb(i), OP_N, MONE, gD(i), ONE, b, U, act));
+    if (k0) {
+      CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U, act, true));
+      ++ctx->launches;
+      CU(antiherm_update(k0->D(i), Wm, b, U, s, act));
+    }
     if (io.GRl) CU(eng.gemm(offB(io.GRl, i), gD(i + 1), OP_N, Yb(i), OP_N, MONE, NOMAT, ZERO, b, U, act));
-    for (const Kind& k : kinds) {
-      const BMat Z = S1(T[1]), P = S1(T[2]), Wm = S1(T[3]);
-      // Z = A_{i+1,i} g^x_i;  P = G^x_{i+1,i+1} X^H;  W = G_{i,i+1} Z   (x = <, >)
+    if (k0 && k0->low)
+      CU(eng.gemm(offB(k0->low, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U, act, io.GRl != nullptr));
+    for (size_t x = 1; x < kinds.size(); ++x) {
+      const Kind& k = kinds[x];
       CU(eng.gemm(Z, S1(Alow), OP_N, k.D(i), OP_N, ONE, NOMAT, ZERO, b, U, act));
       CU(eng.gemm(P, k.D(i + 1), OP_N, X, OP_H, ONE, NOMAT, ZERO, b, U, act));
       CU(eng.gemm(Wm, Gup, OP_N, Z, OP_N, ONE, NOMAT, ZERO, b, U, act));
-      // G^x_ii = g^x_i + X P - W + W^H
       CU(eng.gemm(k.D(i), X, OP_N, P, OP_N, ONE, k.D(i), ONE, b, U, act));
       ++ctx->launches;
       CU(antiherm_update(k.D(i), Wm, b, U, s, act));
-      // G^x_{i+1,i} = -G_{i+1,i+1} Z - P
       if (k.low) CU(eng.gemm(offB(k.low, i), gD(i + 1), OP_N, Z, OP_N, MONE, P, MONE, b, U, act));
     }
   }

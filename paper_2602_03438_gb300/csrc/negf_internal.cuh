@@ -78,6 +78,10 @@ struct GemmArgs {
   int units;           // batch
   const int* active;   // per unit, nullable: 0 => unit skipped
   int plus_identity = 0;   // sliced kernels: D += I after the rest (the residual I - M X in one product)
+  // sliced kernels with n <= 128: op(A)'s scales and digit images are still in the scratch
+  // from the previous product on the same op(A) (same layout, units and mask), so that
+  // only op(B)'s column scales are made before the product
+  int reuse_a = 0;
 };
 
 // ---------------------------------------------------------------------------
