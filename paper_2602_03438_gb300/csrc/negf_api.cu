@@ -2599,15 +2599,15 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
         return NEGF_OK;
       };
       auto lgemm = [&](BMat D, BMat A, int opA, BMat B, int opB, zc alpha, BMat C, zc beta,
-                       const int* mask) -> cudaError_t {
+                       const int* mask, bool reuse_a = false) -> cudaError_t {
         if (ncomp > 0) {
           auto cm = [&](BMat m) {
             if (m.p) m.off = coff;
             return m;
           };
-          return eng.gemm(cm(D), cm(A), opA, cm(B), opB, alpha, cm(C), beta, b, ncomp, nullptr);
+          return eng.gemm(cm(D), cm(A), opA, cm(B), opB, alpha, cm(C), beta, b, ncomp, nullptr, reuse_a);
         }
-        return eng.gemm(D, A, opA, B, opB, alpha, C, beta, b, NU, mask);
+        return eng.gemm(D, A, opA, B, opB, alpha, C, beta, b, NU, mask, reuse_a);
       };
       auto n_set = [&](const int* flags) -> int {
         ++ctx->launches;
@@ -2702,14 +2702,16 @@ negf_status negf_obc(negf_ctx* c, const negf_system* sys, negf_precision prec, d
           }
           if (it == max_iter) break;
           if ((st = lead_inverse(g, eps, act)) != NEGF_OK) return st;        // g = eps^{-1}
+          // the two products of each left operand back to back (the sliced product keeps
+          // its digit images for the second)
           CU(lgemm(T[0], al, OP_N, g, OP_N, ONE, NOMAT, ZERO, act));              // al g
-          CU(lgemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, act));              // be g
           CU(lgemm(T[2], T[0], OP_N, be, OP_N, ONE, NOMAT, ZERO, act));           // al g be
+          CU(lgemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, act, true));    // -al g al
+          CU(lgemm(T[1], be, OP_N, g, OP_N, ONE, NOMAT, ZERO, act));              // be g
           CU(lgemm(T[3], T[1], OP_N, al, OP_N, ONE, NOMAT, ZERO, act));           // be g al
+          CU(lgemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, act, true));    // -be g be
           lead_update_kernel<<<eg, 256, 0, s>>>(eps, epss, T[2], T[3], b, done);
           KCHECK();
-          CU(lgemm(T[4], T[0], OP_N, al, OP_N, MONE, NOMAT, ZERO, act));          // -al g al
-          CU(lgemm(T[5], T[1], OP_N, be, OP_N, MONE, NOMAT, ZERO, act));          // -be g be
           std::swap(al, T[4]);
           std::swap(be, T[5]);
         }
