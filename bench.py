@@ -717,9 +717,14 @@ def run_config4(args):
     if ctx.sync() != 0:
         raise RuntimeError("device status after the config-4 run")
     ms_obc, ms_sw = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    # FP64 sweeps with stored blocks on sampled energies, same Sigma
+    # FP64 sweeps with stored blocks on sampled energies, same Sigma: evenly spaced ones
+    # and the energy where the mixed current peaks (so that the current is checked where
+    # it is largest, not only against the floor of 1e-3 of the grid's largest current)
     k = max(1, min(4 if args.fp64_sample is None else args.fp64_sample, dev.ne))
-    idx = np.linspace(0, dev.ne - 1, k).round().astype(int)
+    J_all = J.cpu().numpy().reshape(dev.ne, dev.nb - 1)
+    j_peak = int(np.abs(J_all).max(axis=1).argmax())
+    idx = np.unique(np.append(np.linspace(0, dev.ne - 1, k).round().astype(int), j_peak))
+    k = len(idx)
     sub = dev.truncated(energies=idx)
     s2 = P.upload(sub)
     o2 = P.allocate_outputs(s2)
@@ -735,15 +740,17 @@ def run_config4(args):
                        o2["current"], None, prec=P.FP64)
     torch.cuda.synchronize()
     J64 = o2["current"].cpu().numpy().reshape(k, dev.nb - 1)
-    Jm = J.cpu().numpy().reshape(dev.ne, dev.nb - 1)[idx]
-    J_grid_max = float(np.abs(J.cpu().numpy()).max())   # max_E over all energies (mixed)
+    Jm = J_all[idx]
+    J_grid_max = float(np.abs(J_all).max())   # max_E over all energies (mixed)
     line = {"workload": "config4", "devices": 1, "energies": dev.ne, "nb": dev.nb, "b": dev.b,
             "mixed": {"value": dev.ne / ((ms_obc + ms_sw) / 1e3), "unit": UNIT, "ms_per_run": ms_obc + ms_sw,
                       "ms_obc": ms_obc, "ms_sweeps_and_observables": ms_sw,
                       "what": "OBC + G^R/G^< sweeps + T, DOS, current, density over all 512 energies, mixed "
                               "precision, blocks kept in the workspace chunk by chunk (negf_rgf_observables)"},
             "J_err_vs_fp64": current_error(Jm, J64, J_grid_max),
-            "fp64_sampled_energies": idx.tolist(),
+            "J_err_at_peak_vs_fp64": float(np.abs(Jm[list(idx).index(j_peak)] - J64[list(idx).index(j_peak)]).max() /
+                                           np.abs(J64[list(idx).index(j_peak)]).max()),
+            "fp64_sampled_energies": idx.tolist(), "current_peak_energy_index": j_peak,
             "finite": bool(np.isfinite(J.cpu().numpy()).all() and np.isfinite(n.cpu().numpy()).all()),
             "status": {"obc_not_converged": int((st_obc != 0).sum().item()),
                        "rgf_flagged": int((status != 0).sum().item())}}

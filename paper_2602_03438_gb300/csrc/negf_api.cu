@@ -601,16 +601,14 @@ struct Engine {
         // thread, so D, A and C may all be X.  I - M X is small (below ~1e-3 when the
         // FP32 inverse is usable at all), so the correction X (I - M X) needs far less
         // than FP64 class: the 5-digit product (15 slice pairs instead of 36, error
-        // ~2^-34 of |X| |I - M X|; 4 digits measured G^R 9e-8 against FP64 at config 2).
-        // Blocks above 128 keep 8 digits: with 5 the current of the b = 512 workload
-        // moved from 4.6e-7 to 5.4e-7 against FP64, close to the 1e-6 bar
+        // ~2^-34 of |X| |I - M X|; 4 digits measured G^R 9e-8 against FP64 at config 2)
         GemmArgs c;
         c.D = X; c.A = X; c.B = T1; c.C = X;
         c.opA = OP_N; c.opB = OP_N; c.alpha = zmake(1.0, 0.0); c.beta = zmake(1.0, 0.0);
         c.n = n; c.units = units; c.active = active;
         const bool masked = active != nullptr && active_frac < 0.0;
-        begin(masked ? K_OTHER : (n <= 128 ? K_GEMM_OZ_LO : K_GEMM_OZ));
-        e = (n <= 128) ? sliced_lo(c) : sliced(c);
+        begin(masked ? K_OTHER : K_GEMM_OZ_LO);
+        e = sliced_lo(c);
         end(masked ? 0.0 : 8.0 * (double)n * n * n * units * frac, masked ? 0.0 : 64.0 * (double)n * n * units * frac);
         if (e != cudaSuccess) return e;
         continue;
