@@ -493,7 +493,12 @@ struct Engine {
     last_a = (e == cudaSuccess && keepable && g.D.p != g.A.p) ? k : AKey();
     return e;
   }
-  cudaError_t sliced_lo(const GemmArgs& g) {   // the 5-digit product: its own images in the scratch
+  // a scratch region of the 5-digit product's own (set by the sweeps for their duration),
+  // so that its images leave the 8-digit product's in place; without it both share
+  // ozt_scratch
+  void* ozt_scratch_lo = nullptr;
+  cudaError_t sliced_lo(const GemmArgs& g) {
+    if (ozt_scratch_lo) return zgemm_ozt_lo(g, ozt_scratch_lo, ctx->d_err, s);
     last_a = AKey();
     return zgemm_ozt_lo(g, ozt_scratch, ctx->d_err, s);
   }
@@ -583,7 +588,9 @@ struct Engine {
         r.alpha = zmake(-1.0, 0.0);
         r.plus_identity = 1;
         begin(K_GEMM_OZ);
-        e = sliced(r);
+        // M is the last step's left operand too: its images are reused when the
+        // correction in between kept to a scratch region of its own
+        e = sliced(r, k > 0);
       } else {
         begin(K_GEMM_F64);
         e = zgemm_f64(r, s);
@@ -695,6 +702,14 @@ negf_status rgf_chunk(Ctx* ctx, Engine& eng, const DevView& dv, const ScatView& 
   }
   p = (char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
   eng.ozt_scratch = (void*)p;
+  // the 5-digit correction products in a region of their own for the duration of the
+  // sweeps (the refinement's residuals then reuse M's images)
+  struct LoScratch {
+    Engine& e;
+    ~LoScratch() { e.ozt_scratch_lo = nullptr; }
+  } lo_guard{eng};
+  if (eng.mixed == 1 && oz_supported(b))
+    eng.ozt_scratch_lo = (void*)(p + ((ozt_scratch_bytes(b, U) + 1023) & ~(size_t)1023));
 
   auto S1 = [&](zc* base) { return BMat{base, bb}; };
   // per-energy output blocks: [e][i] with unit stride nb*b*b (diag) or (nb-1)*b*b (off-diagonal);
@@ -1211,7 +1226,8 @@ size_t rgf_bytes_per_energy(int nb, int b, const RgfIO& io, int mixed) {
   if (!io.GRu) n += 1;
   size_t bytes = n * blk;
   bytes += zinv_scratch_bytes(b, 1, mixed ? 1 : 0);
-  if (mixed == 1) bytes += ozt_scratch_bytes(b, 1) + 1024;
+  // the sliced products' scratch, and a second one for the 5-digit correction products
+  if (mixed == 1) bytes += 2 * (ozt_scratch_bytes(b, 1) + 1024);
   return bytes;
 }
 
