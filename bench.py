@@ -339,6 +339,16 @@ def rel_block_err(a, b, nblk):
     return float((num / den).max())
 
 
+def sample_with_peak(ne, k, J):
+    """Energies for the FP64 comparison: k evenly spaced over the grid of ne (ends
+    included) and the energy where the current J ([ne][interfaces]) is largest in
+    magnitude; sorted, without repeats.  Returns (indices, peak index)."""
+    J = np.asarray(J).reshape(ne, -1)
+    peak = int(np.abs(J).max(axis=1).argmax())
+    idx = np.unique(np.append(np.linspace(0, ne - 1, max(1, min(k, ne))).round().astype(int), peak))
+    return idx, peak
+
+
 def current_error(J_mixed, J_ref, grid_max):
     """The scalar reading of the current's error: max over the sampled energies and
     interfaces of |J_mixed - J_ref| / max(|J_ref|, 1e-3 grid_max), with grid_max the
@@ -464,12 +474,10 @@ def run_gpu(args):
     cmp = {}
     fp64_sample = 128 if args.fp64_sample is None else args.fp64_sample
     if fp64_sample > 0 and rank == 0:
-        k = min(fp64_sample, ne)
-        idx = np.linspace(0, ne - 1, k).round().astype(int)
-        # and the energy where the mixed current peaks, so that the error floor of the
-        # current (1e-3 of its largest value over the grid) is itself checked against FP64
-        j_peak = int(out["current"].view(ne, nb - 1).abs().amax(dim=1).argmax().item())
-        idx = np.unique(np.append(idx, j_peak))
+        # evenly spaced energies and the one where the mixed current peaks, so that the
+        # error floor of the current (1e-3 of its largest value over the grid) is itself
+        # checked against FP64
+        idx, j_peak = sample_with_peak(ne, fp64_sample, out["current"].view(ne, nb - 1).cpu().numpy())
         k = int(idx.size)
         sub = W.config2(nb=args.nb, b=args.b, ne=args.ne)
         sub.energy = dev.energy[idx]
@@ -720,10 +728,8 @@ def run_config4(args):
     # FP64 sweeps with stored blocks on sampled energies, same Sigma: evenly spaced ones
     # and the energy where the mixed current peaks (so that the current is checked where
     # it is largest, not only against the floor of 1e-3 of the grid's largest current)
-    k = max(1, min(4 if args.fp64_sample is None else args.fp64_sample, dev.ne))
     J_all = J.cpu().numpy().reshape(dev.ne, dev.nb - 1)
-    j_peak = int(np.abs(J_all).max(axis=1).argmax())
-    idx = np.unique(np.append(np.linspace(0, dev.ne - 1, k).round().astype(int), j_peak))
+    idx, j_peak = sample_with_peak(dev.ne, 4 if args.fp64_sample is None else args.fp64_sample, J_all)
     k = len(idx)
     sub = dev.truncated(energies=idx)
     s2 = P.upload(sub)

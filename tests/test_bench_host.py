@@ -196,3 +196,23 @@ def test_hbm_bandwidth_from_the_traffic_record():
     h = bench.hbm_for("gemm_oz", peaks, "test")
     gbs = rec["bytes_per_launch_full"] / (rec["ms_per_launch_full"] / 1e3) / 1e9
     assert abs(h["achieved_gbs"] - gbs) < 1e-9 * gbs and abs(h["frac"] - gbs / 6000.0) < 1e-12
+
+
+def test_fp64_sample_includes_the_current_peak():
+    """The FP64 comparison's energies: evenly spaced, ends included, plus the energy of
+    the largest current (once, in order), which a sparse sample would otherwise miss."""
+    ne = 512
+    J = np.zeros((ne, 31))
+    J[261, 7] = -3e-3        # the peak, by magnitude and negative
+    J[10, 0] = 1e-3
+    idx, peak = bench.sample_with_peak(ne, 4, J)
+    assert peak == 261
+    assert idx.tolist() == [0, 170, 261, 341, 511]
+    # a peak that is already a sample point is not repeated
+    J2 = np.zeros((ne, 3))
+    J2[341, 1] = 1.0
+    idx2, peak2 = bench.sample_with_peak(ne, 4, J2)
+    assert peak2 == 341 and idx2.tolist() == [0, 170, 341, 511]
+    # k above ne: every energy once
+    idx3, _ = bench.sample_with_peak(5, 128, np.arange(10.0).reshape(5, 2))
+    assert idx3.tolist() == [0, 1, 2, 3, 4]
