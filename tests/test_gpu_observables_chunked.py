@@ -27,12 +27,15 @@ def P():
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
-def test_chunked_observables_equal_the_stored_path(P, prec):
-    dev = W.small_scattering_device(5, 24, 40, seed=123, overlap=True, strength=0.05)
+@pytest.mark.parametrize("b,ws", [(24, 6 << 20), (8, 256 << 10)])
+def test_chunked_observables_equal_the_stored_path(P, prec, b, ws):
+    """b = 8 runs the one-launch sweep of small blocks chunk by chunk (about 4 energies
+    per chunk in 256 KB)."""
+    dev = W.small_scattering_device(5, b, 40, seed=123, overlap=True, strength=0.05)
     strong_leads(dev, seed=6)
     p = getattr(P, prec)
     big = P.Context(0, 1 << 30)
-    small = P.Context(0, 6 << 20)      # a few energies per chunk
+    small = P.Context(0, ws)           # a few energies per chunk
     try:
         sys_ = P.upload(dev)
         out = P.allocate_outputs(sys_)
