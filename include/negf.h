@@ -69,7 +69,9 @@ typedef enum {
                           row/column scales with the default 8 digits, see
                           negf_sliced_digits; 16 <= b <= 512, K in exact passes of 256;
                           FP64 FMA otherwise); block inverses in FP32 + two refinement
-                          steps whose residual uses the same product; I/O complex128        */
+                          steps whose residual uses the same product and whose correction
+                          a 5-digit one; devices with b < 16 run their sweeps in FP64 (one
+                          launch); I/O complex128                                           */
   NEGF_MIXED_TF32 = 2  /* block products as 3-term TF32 splits (hi*hi + hi*lo + lo*hi) on
                           the tensor cores, FP32 accumulate in TMEM (~1e-6 relative per
                           128-wide product); inverses FP32 + refinement with an FP64
@@ -148,8 +150,10 @@ negf_status negf_worklist(const negf_system* sys, int32_t bs, int32_t* count, in
  * prec: NEGF_FP64 runs every product in FP64; NEGF_MIXED runs the products of the
  * decimation, the residuals and the Newton steps on the digit-sliced BF16 tensor-core
  * path (FP64-class: exact FP32 accumulation of 7-bit slices, ~2^-55 of the row/column
- * scales with 8 digits) when 16 <= b <= 512, keeping every inverse in FP64; NEGF_MIXED_TF32 is
- * treated as NEGF_FP64 (a TF32 product is far too coarse for the 1e-10 residual).
+ * scales with 8 digits) when 16 <= b <= 512, with the inverses in FP32 refined twice (twice
+ * more for units whose refinement residual stays above 1e-7) and redone in FP64 for any unit
+ * still above it; NEGF_MIXED_TF32 is treated as NEGF_FP64 (a TF32 product is far too coarse
+ * for the 1e-10 residual).
  *
  * Warm start (optional, per lead side): with g0_L and/or g0_R given, that side
  * first takes up to 8 plain Newton steps from the guess (each step's Stein
